@@ -1,0 +1,21 @@
+"""Plain FP64 CPU oracle for the batched quantum-trajectory TEBD hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, links or runs
+anything in this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline legs of ``bench.py`` may use it.  It shares no code with the CUDA
+library; both sides receive the same seeded inputs from ``workloads.py``.
+
+Modules
+  philox   counter-based Philox4x32-10 generator (Salmon et al., SC'11), the
+           one random source the trajectory method draws from (Sec. 4.1).
+  model    the free-fermion chain, its jump operators and the two-site
+           effective-Hamiltonian gates (Sec. 2.1, Eqs. Hamiltonian,
+           EffHamiltonian; Sec. 2.3 Trotter splitting).
+  tebd     the MPS quantum-trajectory integrator in Vidal-Hastings form
+           (Sec. 2.3 Eq. Theta, Sec. 4.1 Eqs. QJump1, TransitionRate).
+  dense    brute-force references: the dense Trotterised state vector, dense
+           Lindblad integration of rho, and the correlation-matrix equation of
+           motion (Sec. 2.1 Eqs. eqCorr, SoleqCorr; Eq. Lindblad).
+
+All floating point is float64 / complex128.
+"""

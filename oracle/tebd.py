@@ -1,0 +1,303 @@
+"""MPS quantum-trajectory integrator in Vidal-Hastings form (plain FP64).
+
+State (Sec. 2.2, Eqs. MPS, MPSMixte; Vidal form as in Sec. 2.3): per site a tensor
+B_i = Gamma_i Lambda_i of shape (chi_{i-1}, 2, chi_i), per bond the Schmidt values
+Lambda_i (length chi_i), chi_{-1} = chi_{L-1} = 1, Lambda_{-1} = [1].  The state is
+psi = B_0 B_1 ... B_{L-1}.
+
+Two-site update (Sec. 2.3, Eq. Theta, with the Hastings variant that avoids
+dividing by Lambda):
+  theta~[(a,s'),(t',c)] = sum_{s,t} G[s't',st] sum_m B_b[a,s,m] B_{b+1}[m,t,c]
+  theta = Lambda_{b-1}[a] theta~                      (rows weighted)
+  theta = U S V^+  (SVD, S descending)
+  keep k = min(chi_max, #{S_j > cut * S_0}) >= 1     (keep the chi largest, Sec. 2.2)
+  discarded weight w = sum_{j>=k} S_j^2 / sum_j S_j^2 (Eq. HilbertSchmidtNorm)
+  Lambda_b <- S_k / ||S_k||                            (renormalise, Sec. 2.3 end)
+  B_{b+1} <- V_k^+,  B_b <- theta~ V_k / ||S_k||
+
+One time step of a trajectory (Sec. 4.1, after Eq. ErrorCLT's preceding text):
+  rates W_k = gamma_k <L_k^+ L_k> for every channel (Eq. TransitionRate), with
+  <n_k> = <psi|n_k|psi>/<psi|psi> contracted with left and right environments
+  (equal to the Fig. 3 local formula when the form is exactly canonical);
+  draw r ~ U[0,1) (Philox, purpose 0); if r < P = sum_k W_k dt the channel is the
+  least k with cumulative sum of W dt above r: apply L_k, renormalise and restore
+  the canonical form; otherwise apply the Trotter layers of exp(-i H_eff dt)
+  (Eq. QJump1), the norm being restored by each bond's renormalisation.
+
+Canonical form after a jump: L_k changes only B_k (plus a sign on the occupied
+component of every B_j, j < k, for the fermionic string, a unitary).  Identity-gate
+bond updates at bonds k-1, ..., 1 (right to left) make B_k..B_1 right-canonical,
+then identity-gate updates at bonds 0, ..., L-2 (left to right) restore every
+Lambda as the exact Schmidt spectrum (Sec. 2.2, Eq. ShiftCenter, done by SVD).
+"""
+import numpy as np
+
+from . import model
+from .philox import uniform01, PURPOSE_JUMP
+
+IDENTITY4 = np.eye(4, dtype=complex)
+
+
+class TrajectoryConfig:
+    """Parameters of the trajectory integrator (one chain, many trajectories)."""
+
+    def __init__(self, L, J=1.0, dt=0.05, chi_max=16, svd_cut=1e-12,
+                 gamma_loss=0.0, gamma_gain=0.0, gamma_deph=0.0,
+                 fermionic=True, trotter_order=2, occupation=None, seed=0):
+        self.L = int(L)
+        self.J = float(J)
+        self.dt = float(dt)
+        self.chi_max = int(chi_max)
+        self.svd_cut = float(svd_cut)
+        self.gamma_loss = np.broadcast_to(np.asarray(gamma_loss, float), (L,)).copy()
+        self.gamma_gain = np.broadcast_to(np.asarray(gamma_gain, float), (L,)).copy()
+        self.gamma_deph = np.broadcast_to(np.asarray(gamma_deph, float), (L,)).copy()
+        self.fermionic = bool(fermionic)
+        self.trotter_order = int(trotter_order)
+        self.occupation = (np.zeros(L, int) if occupation is None
+                           else np.asarray(occupation, int).copy())
+        self.seed = int(seed)
+
+    def layers(self):
+        """Trotter schedule as (parity, tau): parity 0 = even bonds, 1 = odd bonds."""
+        dt = self.dt
+        if self.trotter_order == 1:
+            return [(0, dt), (1, dt)]
+        if self.trotter_order == 2:
+            return [(0, dt / 2), (1, dt), (0, dt / 2)]
+        raise ValueError("trotter_order must be 1 or 2")
+
+    def gates(self, tau):
+        return model.bond_gates(self.L, self.J, tau, self.gamma_loss,
+                                self.gamma_gain, self.gamma_deph)
+
+
+class Trajectory:
+    """One MPS history |psi_alpha(t)> in Vidal-Hastings form."""
+
+    def __init__(self, cfg):
+        self.cfg = cfg
+        L = cfg.L
+        self.B = []
+        for i in range(L):
+            t = np.zeros((1, 2, 1), dtype=complex)
+            t[0, int(cfg.occupation[i]), 0] = 1.0
+            self.B.append(t)
+        self.lam = [np.ones(1) for _ in range(L - 1)]
+        self.trunc_weight = 0.0
+
+    @classmethod
+    def from_tensors(cls, cfg, B, lam):
+        self = cls.__new__(cls)
+        self.cfg = cfg
+        self.B = [np.array(b, dtype=complex) for b in B]
+        self.lam = [np.array(x, dtype=float) for x in lam]
+        self.trunc_weight = 0.0
+        return self
+
+    def bond_dims(self):
+        return [len(x) for x in self.lam]
+
+    def left_weight(self, b):
+        return self.lam[b - 1] if b > 0 else np.ones(1)
+
+    # ---- Sec. 2.3, Eq. Theta (Hastings form) --------------------------------
+    def update_bond(self, b, G):
+        cfg = self.cfg
+        Bl, Br = self.B[b], self.B[b + 1]
+        chiL, chiR = Bl.shape[0], Br.shape[2]
+        P = np.tensordot(Bl, Br, axes=(2, 0))                  # [a, s, t, c]
+        tt = np.einsum('uvst,astc->auvc', G.reshape(2, 2, 2, 2), P)
+        tt = tt.reshape(chiL * 2, 2 * chiR)                     # theta~
+        th = tt * np.repeat(self.left_weight(b), 2)[:, None]    # theta
+        U, S, Vh = np.linalg.svd(th, full_matrices=False)
+        if not S[0] > 0.0:
+            raise FloatingPointError("theta vanished at bond %d" % b)
+        k = int(np.count_nonzero(S > cfg.svd_cut * S[0]))
+        k = max(1, min(cfg.chi_max, k))
+        total = float(np.sum(S ** 2))
+        kept = float(np.sum(S[:k] ** 2))
+        norm = np.sqrt(kept)
+        self.trunc_weight += (total - kept) / total
+        Vk_h = Vh[:k]
+        self.B[b + 1] = Vk_h.reshape(k, 2, chiR).copy()
+        self.B[b] = (tt @ Vk_h.conj().T / norm).reshape(chiL, 2, k)
+        self.lam[b] = S[:k] / norm
+
+    def apply_layer(self, parity, gates):
+        for b in range(parity, self.cfg.L - 1, 2):
+            self.update_bond(b, gates[b])
+
+    # ---- expectation values (Fig. 3, with exact environments) ---------------
+    def environments(self):
+        """Left and right transfer-matrix environments of <psi|psi>.
+
+        Lenv[i][b', b] = sum conj(psi-left)_{b'} (psi-left)_b over sites < i,
+        Renv[i][a, a'] = sum over sites >= i, Lenv[0] = Renv[L] = [[1]].
+        Under the non-unitary effective-Hamiltonian gates the bond-parallel
+        update leaves the neighbouring Lambda only approximately canonical, so
+        expectation values contract the full environments instead of assuming
+        Lenv = diag(Lambda^2) and Renv = 1 (they coincide in canonical form)."""
+        L = self.cfg.L
+        Lenv = [None] * (L + 1)
+        Renv = [None] * (L + 1)
+        Lenv[0] = np.ones((1, 1), dtype=complex)
+        Renv[L] = np.ones((1, 1), dtype=complex)
+        for i in range(L):
+            Bi = self.B[i]
+            Lenv[i + 1] = sum(Bi[:, s, :].conj().T @ Lenv[i] @ Bi[:, s, :] for s in range(2))
+        for i in range(L - 1, -1, -1):
+            Bi = self.B[i]
+            Renv[i] = sum(Bi[:, s, :] @ Renv[i + 1] @ Bi[:, s, :].conj().T for s in range(2))
+        return Lenv, Renv
+
+    def norm2(self):
+        return float(np.real(self.environments()[1][0][0, 0]))
+
+    def density(self):
+        """<n_i> = <psi|n_i|psi> / <psi|psi> for every site."""
+        Lenv, Renv = self.environments()
+        nrm = np.real(Renv[0][0, 0])
+        out = np.empty(self.cfg.L)
+        for i in range(self.cfg.L):
+            B1 = self.B[i][:, 1, :]
+            out[i] = np.real(np.sum(B1.conj() * (Lenv[i] @ B1 @ Renv[i + 1]))) / nrm
+        return out
+
+    def channel_rates(self):
+        """W_k = gamma_k <L_k^+ L_k> for channel k = 3 * site + kind (Eq. TransitionRate)."""
+        cfg = self.cfg
+        n = self.density()
+        W = np.zeros(3 * cfg.L)
+        W[0::3] = cfg.gamma_loss * n
+        W[1::3] = cfg.gamma_gain * (1.0 - n)
+        W[2::3] = cfg.gamma_deph * n
+        return W
+
+    def apply_jump(self, channel):
+        """|psi> <- L_k |psi>, then renormalise and restore the canonical form."""
+        cfg = self.cfg
+        site, kind = divmod(int(channel), model.N_KINDS)
+        O = model.jump_operator(kind)
+        self.B[site] = np.einsum('uv,avc->auc', O, self.B[site])
+        if model.has_string(kind, cfg.fermionic):
+            for j in range(site):
+                self.B[j] = self.B[j].copy()
+                self.B[j][:, 1, :] *= -1.0
+        self.recanonicalize(site)
+
+    def recanonicalize(self, site):
+        for b in range(site - 1, 0, -1):
+            self.update_bond(b, IDENTITY4)
+        for b in range(0, self.cfg.L - 1):
+            self.update_bond(b, IDENTITY4)
+
+    # ---- <c_i^+ c_j> by transfer matrices -------------------------------------
+    def correlation(self):
+        """C_ij = <c_i^+ c_j> = <s+_i prod_{i<l<j} (-1)^{n_l} s-_j> / <psi|psi>
+        for i < j, C_ji = conj(C_ij), C_ii = <n_i> (Jordan-Wigner, Sec. 2.1)."""
+        L = self.cfg.L
+        Lenv, Renv = self.environments()
+        nrm = np.real(Renv[0][0, 0])
+        C = np.zeros((L, L), dtype=complex)
+        C[np.diag_indices(L)] = self.density()
+        for i in range(L):
+            Bi = self.B[i]
+            # s+ = |1><0|: bra component 1, ket component 0
+            E = Bi[:, 1, :].conj().T @ Lenv[i] @ Bi[:, 0, :]
+            for j in range(i + 1, L):
+                Bj = self.B[j]
+                # close with s- = |0><1|: bra component 0, ket component 1
+                C[i, j] = np.sum(Bj[:, 0, :].conj() * (E @ Bj[:, 1, :] @ Renv[j + 1])) / nrm
+                C[j, i] = np.conj(C[i, j])
+                # carry the string (-1)^n through site j
+                E = (Bj[:, 0, :].conj().T @ E @ Bj[:, 0, :]
+                     - Bj[:, 1, :].conj().T @ E @ Bj[:, 1, :])
+        return C
+
+    def to_dense(self):
+        """Contract B_0 ... B_{L-1} into the 2^L vector (site 0 most significant)."""
+        v = self.B[0].reshape(2, -1)
+        for i in range(1, self.cfg.L):
+            Bi = self.B[i]
+            v = (v @ Bi.reshape(Bi.shape[0], -1)).reshape(-1, Bi.shape[2])
+        return v.reshape(-1)
+
+
+def draw_channel(rates, dt, r):
+    """Jump-or-evolve decision (Sec. 4.1): -1 if r >= P = sum W dt, else the least
+    channel whose cumulative probability exceeds r."""
+    p = rates * dt
+    total = float(np.sum(p))
+    if total >= 0.5:
+        raise ValueError("jump probability per step %.3g >= 0.5: reduce dt" % total)
+    if not r < total:
+        return -1
+    csum = np.cumsum(p)
+    return int(np.argmax(csum > r))
+
+
+class StepGates:
+    """The gates of one Trotter step, built once per run."""
+
+    def __init__(self, cfg):
+        self.layers = [(parity, cfg.gates(tau)) for parity, tau in cfg.layers()]
+
+
+def step_trajectory(traj, gates, traj_id, step, replay=None):
+    """One time step of one history; returns the applied channel or -1."""
+    cfg = traj.cfg
+    if replay is None or replay == -2:
+        r = uniform01(cfg.seed, traj_id, step, PURPOSE_JUMP)
+        ch = draw_channel(traj.channel_rates(), cfg.dt, r)
+    else:
+        ch = int(replay)
+    if ch >= 0:
+        traj.apply_jump(ch)
+    else:
+        for parity, g in gates.layers:
+            traj.apply_layer(parity, g)
+    return ch
+
+
+def run_trajectories(cfg, n_steps, traj_ids, replay=None, measure_corr=False,
+                     initial=None):
+    """Integrate the histories traj_ids for n_steps steps.
+
+    replay: optional array [len(traj_ids), n_steps] of channels (-1 none, -2 draw).
+    initial: optional list of (B, lam) per trajectory (default: the product state).
+    Returns dict(density [n, L], corr [n, L, L] or None, jumps [n, n_steps],
+    trunc [n], bond_dims [n, L-1]).
+    """
+    gates = StepGates(cfg)
+    n = len(traj_ids)
+    dens = np.zeros((n, cfg.L))
+    corr = np.zeros((n, cfg.L, cfg.L), dtype=complex) if measure_corr else None
+    jumps = np.full((n, n_steps), -1, dtype=np.int64)
+    trunc = np.zeros(n)
+    dims = np.zeros((n, cfg.L - 1), dtype=np.int64)
+    for idx, tid in enumerate(traj_ids):
+        if initial is None:
+            traj = Trajectory(cfg)
+        else:
+            traj = Trajectory.from_tensors(cfg, *initial[idx])
+        for step in range(n_steps):
+            rep = None if replay is None else replay[idx][step]
+            jumps[idx, step] = step_trajectory(traj, gates, tid, step, rep)
+        dens[idx] = traj.density()
+        if measure_corr:
+            corr[idx] = traj.correlation()
+        trunc[idx] = traj.trunc_weight
+        dims[idx] = traj.bond_dims()
+    return dict(density=dens, corr=corr, jumps=jumps, trunc=trunc, bond_dims=dims)
+
+
+def ensemble_stats(values):
+    """Monte Carlo mean and its CLT error sqrt(var / n_conf) (Eq. ErrorCLT)."""
+    values = np.asarray(values)
+    n = values.shape[0]
+    mean = values.mean(axis=0)
+    if n < 2:
+        return mean, np.zeros_like(np.real(mean))
+    var = np.mean(np.abs(values - mean) ** 2, axis=0)
+    return mean, np.sqrt(var / n)
