@@ -1,0 +1,181 @@
+/*
+ * lindtebd.h -- C ABI of the batched quantum-trajectory TEBD library (sm_103a).
+ *
+ * The library integrates many independent quantum trajectories of the Lindblad
+ * equation (Sec. 4.1, Eqs. QJump1, QJump2, MasterEq, TransitionRate) for a
+ * one-dimensional chain whose histories are matrix product states in
+ * Vidal-Hastings form (Sec. 2.2-2.3).  The hot operation is the two-site TEBD
+ * update of Sec. 2.3 (Eq. Theta): contract Lambda_{b-1} B_b B_{b+1} with the
+ * two-site gate exp(-i h_b^eff tau) into theta, take a truncated SVD back to
+ * chi_max and renormalise (Sec. 2.3, Eq. TruncationErr and the normalisation
+ * that follows it).
+ *
+ * Conventions shared by every entry point
+ *  - Sites 0..L-1, bond b joins sites b and b+1, single-site basis |0> empty,
+ *    |1> occupied, two-site index s_b * 2 + s_{b+1}.
+ *  - Every pointer argument is caller-owned HOST memory unless stated; inputs
+ *    are copied before the call returns.  The library owns all device memory
+ *    of a context (allocated in lt_create, freed in lt_destroy).
+ *  - Work is queued on the context's CUDA stream; lt_measure_*, lt_get_*,
+ *    lt_set_state/lt_get_state and lt_save/lt_load synchronise that stream.
+ *  - Every call returns an lt_status.  LT_ERR_NUMERICAL and LT_ERR_TIMEOUT
+ *    poison the context: later calls return LT_ERR_STATE until lt_destroy.
+ *    No call throws, exits or traps the GPU.  lt_last_error() describes the
+ *    most recent failure of a context.
+ *  - Contexts are independent; one context per stream.
+ */
+#ifndef LINDTEBD_H
+#define LINDTEBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lt_ctx_s* lt_ctx;
+
+typedef enum {
+  LT_OK = 0,
+  LT_ERR_ARG = 1,         /* invalid argument or configuration            */
+  LT_ERR_OOM = 2,         /* device allocation failed                     */
+  LT_ERR_CUDA = 3,        /* a CUDA runtime call failed                   */
+  LT_ERR_NUMERICAL = 4,   /* theta vanished, or jump probability >= 0.5   */
+  LT_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out           */
+  LT_ERR_STATE = 6,       /* context poisoned by an earlier error         */
+  LT_ERR_UNSUPPORTED = 7  /* method or option not built                   */
+} lt_status;
+
+typedef enum { LT_TRAJ = 0, LT_QSD = 1, LT_MPDO = 2, LT_PURIFIED = 3 } lt_method;
+
+/* LT_FP64: every step in double precision.  LT_MIXED: site tensors, theta and
+ * the Jacobi rotations in single precision; singular values, the truncation
+ * weight, the renormalisation, the Schmidt values Lambda and the jump
+ * probabilities in double precision. */
+typedef enum { LT_FP64 = 0, LT_MIXED = 1 } lt_precision;
+
+typedef enum {
+  LT_INIT_VACUUM = 0,       /* all sites empty (Sec. 2.1 initial state)      */
+  LT_INIT_NEEL = 1,         /* site i occupied iff i is even                  */
+  LT_INIT_DOMAIN_WALL = 2,  /* sites 0..L/2-1 occupied                        */
+  LT_INIT_PRODUCT = 3       /* occupations from product_occ                   */
+} lt_init;
+
+typedef struct {
+  int32_t L;                 /* chain length, 2 <= L <= 1024                       */
+  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 64             */
+  int32_t n_traj;            /* trajectories held by this context, >= 1            */
+  int32_t kraus_dim;         /* unused by LT_TRAJ (purified method), set 0         */
+  int32_t method;            /* lt_method; only LT_TRAJ is built                   */
+  int32_t precision;         /* lt_precision                                       */
+  int32_t init;              /* lt_init                                            */
+  int32_t trotter_order;     /* 1: A(dt) B(dt); 2: A(dt/2) B(dt) A(dt/2)           */
+  const uint8_t* product_occ;/* [L] 0/1, read for LT_INIT_PRODUCT only; copied      */
+  double J;                  /* hopping amplitude, H = -J sum (c+_{i+1} c_i + h.c.) */
+  double dt;                 /* time step                                          */
+  const double* gamma_loss;  /* [L] rates of L = c_i, NULL = all zero; copied       */
+  const double* gamma_gain;  /* [L] rates of L = c_i^+, NULL = all zero; copied     */
+  const double* gamma_deph;  /* [L] rates of L = n_i, NULL = all zero; copied       */
+  int32_t fermionic_jumps;   /* 1: c_i carries the Jordan-Wigner string; 0: spin   */
+  int32_t max_sweeps;        /* Jacobi sweep limit per SVD, 0 = default (40)       */
+  double svd_cut;            /* keep singular values > svd_cut * largest           */
+  uint64_t seed;             /* Philox4x32-10 key                                  */
+  int64_t traj_offset;       /* global id of trajectory 0 (Philox counter word 0)  */
+  double jacobi_tol;         /* rotate a row pair while |x.y^+| > tol |x| |y|;     */
+                             /* 0 = default 4 eps sqrt(n) of the working precision */
+} lt_config;
+
+/* Create a context: validate cfg, allocate the ensemble on the current device
+ * and set every trajectory to the initial product state (Sec. 4.1: the
+ * initial pure state is an eigenvector of rho(0), here a product state).
+ * stream: a cudaStream_t, or NULL for a stream the context creates and owns.
+ * On success *out holds the context; on failure *out is NULL. */
+lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out);
+
+/* Free every device buffer of the context (and its stream if it owns one). */
+lt_status lt_destroy(lt_ctx ctx);
+
+/* One Trotter layer (Sec. 2.3): apply G_b(tau) = exp(-i h_b^eff tau) by the
+ * two-site update at every bond b with b % 2 == parity, for every trajectory
+ * not marked as jumped by the last lt_apply_jumps (all trajectories before
+ * the first call).  h_b^eff carries half of each bulk site's dissipator
+ * -(i/2) sum_k gamma_k L_k^+ L_k and the whole of an end site's (Eq.
+ * EffHamiltonian, split as in Eq. LindbladLocal).  Gates are built on the host
+ * in double precision once per distinct tau. */
+lt_status lt_apply_layer(lt_ctx ctx, int32_t parity, double tau);
+
+/* Jump-or-evolve decision of time step `step` (Sec. 4.1): for every
+ * trajectory compute W_k = gamma_k <L_k^+ L_k> for the channels k = 3 * site
+ * + kind (kind 0 loss, 1 gain, 2 dephasing; Eq. TransitionRate) with exact
+ * environment contractions, draw r from Philox4x32-10 with counter
+ * (traj_offset + traj, step, 0, step >> 32) and key seed, and jump iff
+ * r < P = sum_k W_k dt, to the least channel whose cumulative W dt exceeds r.
+ * A jump applies L_k (and the string for fermionic loss/gain), renormalises
+ * and restores the canonical form; the trajectory then skips this step's
+ * layers.  replay: [n_traj] forced channels (-1 none, -2 draw), or NULL to
+ * draw for every trajectory.  out_channel: [n_traj] receives the channel
+ * (-1 = no jump), or NULL.  Returns LT_ERR_NUMERICAL if some P >= 0.5. */
+lt_status lt_apply_jumps(lt_ctx ctx, int64_t step, const int32_t* replay,
+                         int32_t* out_channel);
+
+/* QSD noise (Sec. 4.2): not built, returns LT_ERR_UNSUPPORTED. */
+lt_status lt_apply_noise(lt_ctx ctx, int64_t step);
+
+/* n_steps full time steps: lt_apply_jumps(step, NULL, NULL) then the layers
+ * of the configured Trotter order, with step counting on from the context's
+ * step counter (starting at 0). */
+lt_status lt_step(lt_ctx ctx, int32_t n_steps);
+
+/* Ensemble density <n_i> = <psi|n_i|psi>/<psi|psi> (exact environments).
+ * mean: [L] average over trajectories; sem: [L] CLT error sqrt(var/n_traj)
+ * (Eq. ErrorCLT), or NULL; per_traj: [n_traj * L] row-major, or NULL. */
+lt_status lt_measure_density(lt_ctx ctx, double* mean, double* sem, double* per_traj);
+
+/* Correlation matrix C_ij = <c_i^+ c_j> (Sec. 2.1) by transfer matrices with
+ * the Jordan-Wigner string.  C_re/C_im: [L * L] row-major ensemble mean;
+ * per_traj_re/per_traj_im: [n_traj * L * L] or NULL. */
+lt_status lt_measure_corr(lt_ctx ctx, double* C_re, double* C_im,
+                          double* per_traj_re, double* per_traj_im);
+
+/* trunc_weight: [n_traj] accumulated discarded weight sum_{a>k} S_a^2 / sum S^2
+ * (Eq. HilbertSchmidtNorm), or NULL.  bond_dims: [n_traj * (L-1)] or NULL. */
+lt_status lt_get_stats(lt_ctx ctx, double* trunc_weight, int32_t* bond_dims);
+
+/* Replace / read trajectories traj0 .. traj0+n-1.  Layout per trajectory:
+ * dims [L-1] int32; lam [(L-1) * chi_max] double, bond b at b * chi_max;
+ * B [L * 2 * chi_max^2] complex128 as interleaved (re, im) doubles, site i at
+ * i * 2 * chi_max^2, holding B_i[a][s][c] row-major over its actual shape
+ * (chi_{i-1}, 2, chi_i).  Dimensions must satisfy 1 <= chi_b <= chi_max.
+ * lt_set_state also clears the truncation accumulators of those trajectories. */
+lt_status lt_set_state(lt_ctx ctx, int32_t traj0, int32_t n, const int32_t* dims,
+                       const double* lam, const double* B);
+lt_status lt_get_state(lt_ctx ctx, int32_t traj0, int32_t n, int32_t* dims,
+                       double* lam, double* B);
+
+/* Checkpoint / resume: write or read the whole ensemble, the step counter and
+ * the truncation accumulators to or from a file.  Philox draws are keyed by
+ * (trajectory, step), so a resumed run is bit-identical to an uninterrupted one. */
+lt_status lt_save(lt_ctx ctx, const char* path);
+lt_status lt_load(lt_ctx ctx, const char* path);
+
+/* Diagnostics: sweep_hist [64] receives how many SVDs took s Jacobi sweeps
+ * (index s, the last bin collects s >= 63) since the context was created or
+ * the histogram was last cleared; clear != 0 resets it after reading. */
+lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear);
+
+/* Number of kernels this context has launched so far. */
+int64_t lt_launch_count(lt_ctx ctx);
+
+/* The context's CUDA stream (a cudaStream_t). */
+void* lt_stream(lt_ctx ctx);
+
+/* Current step counter of the context. */
+int64_t lt_get_step(lt_ctx ctx);
+
+const char* lt_status_str(lt_status s);
+const char* lt_last_error(lt_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LINDTEBD_H */

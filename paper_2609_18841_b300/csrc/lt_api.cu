@@ -1,0 +1,585 @@
+// Host side of the lindtebd C ABI: configuration checks, context memory,
+// two-site gate construction and the order of kernel launches of a time step.
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <new>
+
+#include "lt_internal.cuh"
+
+cudaError_t configure_bond(lt_ctx_s* c);
+
+namespace {
+
+typedef std::complex<double> cd;
+
+#define LT_CK(call)                                                               \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) return fail(c, LT_ERR_CUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+lt_status fail(lt_ctx_s* c, lt_status s, const char* what, const char* why) {
+  if (c) {
+    c->last_error = std::string(what) + ": " + why;
+    if (s == LT_ERR_NUMERICAL || s == LT_ERR_TIMEOUT || s == LT_ERR_CUDA) c->poisoned = true;
+  }
+  return s;
+}
+
+// 4x4 complex matrix helpers (row-major)
+struct M4 {
+  cd v[16];
+};
+M4 mmul(const M4& a, const M4& b) {
+  M4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cd s = 0;
+      for (int k = 0; k < 4; ++k) s += a.v[i * 4 + k] * b.v[k * 4 + j];
+      r.v[i * 4 + j] = s;
+    }
+  return r;
+}
+
+// exp(A) by scaling and squaring of a Taylor series (Sec. 2.3: the two-site
+// exponential "by series expansion"): halve A until its 1-norm is below 1/2,
+// sum the series until the terms drop below 1e-18, square back.
+M4 expm4(M4 A) {
+  double nrm = 0.0;
+  for (int j = 0; j < 4; ++j) {
+    double col = 0.0;
+    for (int i = 0; i < 4; ++i) col += std::abs(A.v[i * 4 + j]);
+    nrm = col > nrm ? col : nrm;
+  }
+  int s = 0;
+  while (nrm > 0.5) {
+    nrm *= 0.5;
+    ++s;
+  }
+  const double scale = std::ldexp(1.0, -s);
+  for (auto& x : A.v) x *= scale;
+  M4 E, term;
+  for (int i = 0; i < 16; ++i) E.v[i] = term.v[i] = (i % 5 == 0) ? 1.0 : 0.0;
+  for (int n = 1; n < 40; ++n) {
+    term = mmul(term, A);
+    double mx = 0.0;
+    for (auto& x : term.v) {
+      x /= (double)n;
+      mx = std::abs(x) > mx ? std::abs(x) : mx;
+    }
+    for (int i = 0; i < 16; ++i) E.v[i] += term.v[i];
+    if (mx < 1e-18) break;
+  }
+  for (int k = 0; k < s; ++k) E = mmul(E, E);
+  return E;
+}
+
+// G_b(tau) = exp(-i tau h_b^eff), h_b^eff = -J (s+ s- + s- s+)
+//   - (i/2) (w_l K_b(s_b) + w_r K_{b+1}(s_{b+1})),  K(s) = loss s + gain (1-s) + deph s,
+// w = 1 for a chain end, 1/2 in the bulk (Eq. EffHamiltonian split per bond).
+void build_gates(const lt_ctx_s* c, double tau, std::vector<double2>& out) {
+  const int L = c->L;
+  out.assign((size_t)(L - 1) * 16, make_double2(0, 0));
+  for (int b = 0; b < L - 1; ++b) {
+    const double wl = b == 0 ? 1.0 : 0.5, wr = b + 1 == L - 1 ? 1.0 : 0.5;
+    M4 h;
+    for (auto& x : h.v) x = 0;
+    h.v[2 * 4 + 1] = -c->J;  // |10><01|
+    h.v[1 * 4 + 2] = -c->J;  // |01><10|
+    for (int sb = 0; sb < 2; ++sb)
+      for (int sc = 0; sc < 2; ++sc) {
+        const double Kl = c->gl[b] * sb + c->gg[b] * (1 - sb) + c->gd[b] * sb;
+        const double Kr = c->gl[b + 1] * sc + c->gg[b + 1] * (1 - sc) + c->gd[b + 1] * sc;
+        h.v[(sb * 2 + sc) * 5] += cd(0.0, -0.5 * (wl * Kl + wr * Kr));
+      }
+    M4 A;
+    for (int i = 0; i < 16; ++i) A.v[i] = cd(0.0, -tau) * h.v[i];
+    const M4 G = expm4(A);
+    for (int i = 0; i < 16; ++i) out[(size_t)b * 16 + i] = make_double2(G.v[i].real(), G.v[i].imag());
+  }
+}
+
+lt_status gate_ptr(lt_ctx_s* c, double tau, const double2** out) {
+  for (size_t i = 0; i < c->gate_taus.size(); ++i)
+    if (c->gate_taus[i] == tau) {
+      *out = c->gates + i * (size_t)(c->L - 1) * 16;
+      return LT_OK;
+    }
+  if (c->gate_taus.size() >= 8) return fail(c, LT_ERR_ARG, "lt_apply_layer", "more than 8 distinct tau values");
+  std::vector<double2> h;
+  build_gates(c, tau, h);
+  const size_t i = c->gate_taus.size();
+  double2* dst = c->gates + i * (size_t)(c->L - 1) * 16;
+  LT_CK(cudaMemcpy(dst, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  c->gate_taus.push_back(tau);
+  *out = dst;
+  return LT_OK;
+}
+
+lt_status check_device_error(lt_ctx_s* c) {
+  int err = 0;
+  LT_CK(cudaMemcpyAsync(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
+  if (err & LT_EBIT_THETA_ZERO) return fail(c, LT_ERR_NUMERICAL, "bond update", "theta vanished");
+  if (err & LT_EBIT_PROB)
+    return fail(c, LT_ERR_NUMERICAL, "jump decision", "jump probability per step >= 0.5; reduce dt");
+  if (err & LT_EBIT_BADARG) {
+    c->last_error = "replayed channel out of range";
+    int zero = 0;
+    LT_CK(cudaMemcpy(c->err_dev, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return LT_ERR_ARG;
+  }
+  return LT_OK;
+}
+
+template <typename T> lt_status dalloc(lt_ctx_s* c, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, LT_ERR_OOM, "cudaMalloc", cudaGetErrorString(e));
+  }
+  return LT_OK;
+}
+
+void free_all(lt_ctx_s* c) {
+  void* ptrs[] = {c->B, c->lam, c->dims, c->trunc, c->evolve, c->channel, c->replay,
+                  c->active_list, c->jumped_list, c->counts, c->density, c->rates, c->gam,
+                  c->err_dev, c->sweep_hist, c->gates, c->bond_scratch, c->env_scratch,
+                  c->corr, c->red};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+lt_status guard(lt_ctx_s* c) {
+  if (!c) return LT_ERR_ARG;
+  if (c->poisoned) return LT_ERR_STATE;
+  return LT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lt_status_str(lt_status s) {
+  switch (s) {
+    case LT_OK: return "ok";
+    case LT_ERR_ARG: return "invalid argument";
+    case LT_ERR_OOM: return "device out of memory";
+    case LT_ERR_CUDA: return "CUDA error";
+    case LT_ERR_NUMERICAL: return "numerical failure";
+    case LT_ERR_TIMEOUT: return "device wait timed out";
+    case LT_ERR_STATE: return "context poisoned by an earlier error";
+    case LT_ERR_UNSUPPORTED: return "unsupported method or option";
+  }
+  return "unknown status";
+}
+
+const char* lt_last_error(lt_ctx ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int64_t lt_launch_count(lt_ctx ctx) { return ctx ? ctx->launches : 0; }
+
+lt_status lt_get_sweep_histogram(lt_ctx c, int32_t* hist, int32_t clear) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (hist) LT_CK(cudaMemcpyAsync(hist, c->sweep_hist, 64 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (clear) LT_CK(cudaMemsetAsync(c->sweep_hist, 0, 64 * sizeof(int), c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
+  return LT_OK;
+}
+
+void* lt_stream(lt_ctx ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int64_t lt_get_step(lt_ctx ctx) { return ctx ? ctx->step_counter : 0; }
+
+lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
+  if (!out) return LT_ERR_ARG;
+  *out = nullptr;
+  if (!cfg) return LT_ERR_ARG;
+  if (cfg->method != LT_TRAJ) return LT_ERR_UNSUPPORTED;
+  if (cfg->L < 2 || cfg->L > 1024 || cfg->chi_max < 1 || cfg->chi_max > LT_MAX_CHI ||
+      cfg->n_traj < 1 || (cfg->precision != LT_FP64 && cfg->precision != LT_MIXED) ||
+      (cfg->trotter_order != 1 && cfg->trotter_order != 2) || !(cfg->dt > 0.0) ||
+      !(cfg->svd_cut >= 0.0) || cfg->max_sweeps < 0 || cfg->max_sweeps > 1000 ||
+      !(cfg->jacobi_tol >= 0.0 && cfg->jacobi_tol < 1.0) || cfg->init < LT_INIT_VACUUM || cfg->init > LT_INIT_PRODUCT ||
+      (cfg->init == LT_INIT_PRODUCT && !cfg->product_occ) || !std::isfinite(cfg->J))
+    return LT_ERR_ARG;
+  lt_ctx_s* c = new (std::nothrow) lt_ctx_s();
+  if (!c) return LT_ERR_OOM;
+  const int L = cfg->L;
+  c->L = L;
+  c->chi = cfg->chi_max;
+  c->n_traj = cfg->n_traj;
+  c->prec = cfg->precision;
+  c->order = cfg->trotter_order;
+  c->fermionic = cfg->fermionic_jumps ? 1 : 0;
+  c->J = cfg->J;
+  c->dt = cfg->dt;
+  c->cut = cfg->svd_cut;
+  c->max_sweeps = cfg->max_sweeps > 0 ? cfg->max_sweeps : 40;
+  c->jacobi_tol = cfg->jacobi_tol;
+  c->seed = cfg->seed;
+  c->traj_offset = cfg->traj_offset;
+  c->init = cfg->init;
+  c->gl.assign(L, 0.0);
+  c->gg.assign(L, 0.0);
+  c->gd.assign(L, 0.0);
+  for (int i = 0; i < L; ++i) {
+    if (cfg->gamma_loss) c->gl[i] = cfg->gamma_loss[i];
+    if (cfg->gamma_gain) c->gg[i] = cfg->gamma_gain[i];
+    if (cfg->gamma_deph) c->gd[i] = cfg->gamma_deph[i];
+    if (!(c->gl[i] >= 0.0) || !(c->gg[i] >= 0.0) || !(c->gd[i] >= 0.0)) {
+      delete c;
+      return LT_ERR_ARG;
+    }
+  }
+  c->occ.assign(L, 0);
+  for (int i = 0; i < L; ++i) {
+    switch (cfg->init) {
+      case LT_INIT_VACUUM: c->occ[i] = 0; break;
+      case LT_INIT_NEEL: c->occ[i] = (i % 2 == 0); break;
+      case LT_INIT_DOMAIN_WALL: c->occ[i] = (i < L / 2); break;
+      default: c->occ[i] = cfg->product_occ[i] ? 1 : 0;
+    }
+  }
+  c->slot = 2 * c->chi * c->chi;
+  c->celt = c->prec == LT_MIXED ? sizeof(float2) : sizeof(double2);
+  lt_status st = LT_OK;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return LT_ERR_CUDA;
+  }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return LT_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  const size_t nt = c->n_traj, nb = L - 1;
+  e = configure_bond(c);
+  if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "configure_bond", cudaGetErrorString(e));
+  c->env_grid = 2 * c->num_sms < c->n_traj ? 2 * c->num_sms : c->n_traj;
+  c->env_scratch_stride = (long long)env_scratch_elems(L, c->chi);
+  if (st == LT_OK) st = dalloc(c, (char**)&c->B, nt * L * c->slot * c->celt);
+  if (st == LT_OK) st = dalloc(c, &c->lam, nt * nb * c->chi);
+  if (st == LT_OK) st = dalloc(c, &c->dims, nt * nb);
+  if (st == LT_OK) st = dalloc(c, &c->trunc, nt * nb);
+  if (st == LT_OK) st = dalloc(c, &c->evolve, nt);
+  if (st == LT_OK) st = dalloc(c, &c->channel, nt);
+  if (st == LT_OK) st = dalloc(c, &c->replay, nt);
+  if (st == LT_OK) st = dalloc(c, &c->active_list, nt);
+  if (st == LT_OK) st = dalloc(c, &c->jumped_list, nt);
+  if (st == LT_OK) st = dalloc(c, &c->counts, 2);
+  if (st == LT_OK) st = dalloc(c, &c->density, nt * L);
+  if (st == LT_OK) st = dalloc(c, &c->rates, nt * 3 * L);
+  if (st == LT_OK) st = dalloc(c, &c->gam, 3 * (size_t)L);
+  if (st == LT_OK) st = dalloc(c, &c->err_dev, 1);
+  if (st == LT_OK) st = dalloc(c, &c->sweep_hist, 64);
+  if (st == LT_OK) st = dalloc(c, &c->gates, 8 * nb * 16);
+  if (st == LT_OK) st = dalloc(c, &c->red, 2 * (size_t)L * L + 2 * (size_t)L);
+  if (st == LT_OK && !c->bond_use_smem)
+    st = dalloc(c, (char**)&c->bond_scratch, (size_t)c->bond_grid * c->bond_scratch_stride * c->celt);
+  if (st == LT_OK)
+    st = dalloc(c, (char**)&c->env_scratch, (size_t)c->env_grid * c->env_scratch_stride * c->celt);
+  uint8_t* occ_dev = nullptr;
+  if (st == LT_OK) st = dalloc(c, &occ_dev, L);
+  if (st == LT_OK) {
+    std::vector<double> g(3 * (size_t)L);
+    for (int i = 0; i < L; ++i) {
+      g[i] = c->gl[i];
+      g[L + i] = c->gg[i];
+      g[2 * L + i] = c->gd[i];
+    }
+    e = cudaMemcpy(c->gam, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(occ_dev, c->occ.data(), L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->B, 0, nt * L * c->slot * c->celt, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->lam, 0, nt * nb * c->chi * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sweep_hist, 0, 64 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_init_state(c, occ_dev);
+    if (e == cudaSuccess) e = launch_compact(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_create", cudaGetErrorString(e));
+  }
+  if (occ_dev) cudaFree(occ_dev);
+  if (st != LT_OK) {
+    free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return LT_OK;
+}
+
+lt_status lt_destroy(lt_ctx c) {
+  if (!c) return LT_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return LT_OK;
+}
+
+lt_status lt_apply_layer(lt_ctx c, int32_t parity, double tau) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if ((parity != 0 && parity != 1) || !std::isfinite(tau)) return LT_ERR_ARG;
+  if (parity > c->L - 2) return LT_OK;
+  const double2* g = nullptr;
+  st = gate_ptr(c, tau, &g);
+  if (st != LT_OK) return st;
+  const int nb = (c->L - 2 - parity) / 2 + 1;
+  LT_CK(launch_bond(c, c->active_list, c->counts, parity, nb, g, 0));
+  return LT_OK;
+}
+
+lt_status lt_apply_jumps(lt_ctx c, int64_t step, const int32_t* replay, int32_t* out_channel) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (step < 0) return LT_ERR_ARG;
+  if (replay)
+    LT_CK(cudaMemcpyAsync(c->replay, replay, sizeof(int) * c->n_traj, cudaMemcpyHostToDevice, c->stream));
+  LT_CK(launch_env(c, 1, step, replay ? c->replay : nullptr));
+  LT_CK(launch_compact(c));
+  LT_CK(launch_jump_apply(c));
+  // restore the canonical form of the jumped histories: right to left over
+  // bonds site-1 .. 1, then left to right over every bond (identity gate)
+  for (int b = c->L - 2; b >= 1; --b) LT_CK(launch_bond(c, c->jumped_list, c->counts + 1, b, 1, nullptr, 1));
+  for (int b = 0; b <= c->L - 2; ++b) LT_CK(launch_bond(c, c->jumped_list, c->counts + 1, b, 1, nullptr, 0));
+  if (replay) {
+    st = check_device_error(c);
+    if (st != LT_OK) return st;
+  }
+  if (out_channel) {
+    LT_CK(cudaMemcpyAsync(out_channel, c->channel, sizeof(int) * c->n_traj, cudaMemcpyDeviceToHost, c->stream));
+    st = check_device_error(c);
+    if (st != LT_OK) return st;
+  }
+  return LT_OK;
+}
+
+lt_status lt_apply_noise(lt_ctx c, int64_t) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  c->last_error = "quantum state diffusion is not built";
+  return LT_ERR_UNSUPPORTED;
+}
+
+lt_status lt_step(lt_ctx c, int32_t n_steps) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (n_steps < 0) return LT_ERR_ARG;
+  for (int s = 0; s < n_steps; ++s) {
+    st = lt_apply_jumps(c, c->step_counter, nullptr, nullptr);
+    if (st != LT_OK) return st;
+    if (c->order == 1) {
+      if ((st = lt_apply_layer(c, 0, c->dt)) != LT_OK) return st;
+      if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
+    } else {
+      if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
+      if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
+      if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
+    }
+    c->step_counter++;
+  }
+  return LT_OK;
+}
+
+lt_status lt_measure_density(lt_ctx c, double* mean, double* sem, double* per_traj) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  LT_CK(launch_env(c, 0, 0, nullptr));
+  LT_CK(launch_reduce_density(c, c->red, c->red + c->L));
+  if (mean) LT_CK(cudaMemcpyAsync(mean, c->red, sizeof(double) * c->L, cudaMemcpyDeviceToHost, c->stream));
+  if (sem) LT_CK(cudaMemcpyAsync(sem, c->red + c->L, sizeof(double) * c->L, cudaMemcpyDeviceToHost, c->stream));
+  if (per_traj)
+    LT_CK(cudaMemcpyAsync(per_traj, c->density, sizeof(double) * c->L * (size_t)c->n_traj,
+                          cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);
+}
+
+lt_status lt_measure_corr(lt_ctx c, double* C_re, double* C_im, double* per_re, double* per_im) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  const size_t LL = (size_t)c->L * c->L;
+  if (!c->corr) {
+    st = dalloc(c, &c->corr, LL * c->n_traj);
+    if (st != LT_OK) return st;
+  }
+  LT_CK(launch_corr(c));
+  LT_CK(launch_reduce_corr(c, c->red));
+  std::vector<double> m(2 * LL);
+  LT_CK(cudaMemcpyAsync(m.data(), c->red, sizeof(double) * 2 * LL, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double2> per;
+  if (per_re || per_im) {
+    per.resize(LL * c->n_traj);
+    LT_CK(cudaMemcpyAsync(per.data(), c->corr, sizeof(double2) * per.size(), cudaMemcpyDeviceToHost, c->stream));
+  }
+  st = check_device_error(c);
+  if (st != LT_OK) return st;
+  for (size_t i = 0; i < LL; ++i) {
+    if (C_re) C_re[i] = m[2 * i];
+    if (C_im) C_im[i] = m[2 * i + 1];
+  }
+  for (size_t i = 0; i < per.size(); ++i) {
+    if (per_re) per_re[i] = per[i].x;
+    if (per_im) per_im[i] = per[i].y;
+  }
+  return LT_OK;
+}
+
+lt_status lt_get_stats(lt_ctx c, double* trunc_weight, int32_t* bond_dims) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  const size_t nb = c->L - 1, nt = c->n_traj;
+  std::vector<double> tr;
+  if (trunc_weight) {
+    tr.resize(nt * nb);
+    LT_CK(cudaMemcpyAsync(tr.data(), c->trunc, sizeof(double) * tr.size(), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (bond_dims)
+    LT_CK(cudaMemcpyAsync(bond_dims, c->dims, sizeof(int) * nt * nb, cudaMemcpyDeviceToHost, c->stream));
+  st = check_device_error(c);
+  if (st != LT_OK) return st;
+  for (size_t t = 0; trunc_weight && t < nt; ++t) {
+    double s = 0.0;
+    for (size_t b = 0; b < nb; ++b) s += tr[t * nb + b];
+    trunc_weight[t] = s;
+  }
+  return LT_OK;
+}
+
+lt_status lt_set_state(lt_ctx c, int32_t traj0, int32_t n, const int32_t* dims, const double* lam,
+                       const double* B) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (traj0 < 0 || n < 0 || traj0 + (long long)n > c->n_traj || !dims || !lam || !B) return LT_ERR_ARG;
+  const size_t nb = c->L - 1;
+  for (size_t i = 0; i < (size_t)n * nb; ++i)
+    if (dims[i] < 1 || dims[i] > c->chi) return LT_ERR_ARG;
+  LT_CK(cudaStreamSynchronize(c->stream));
+  LT_CK(cudaMemcpy(c->dims + (size_t)traj0 * nb, dims, sizeof(int) * n * nb, cudaMemcpyHostToDevice));
+  LT_CK(cudaMemcpy(c->lam + (size_t)traj0 * nb * c->chi, lam, sizeof(double) * n * nb * c->chi,
+                   cudaMemcpyHostToDevice));
+  LT_CK(cudaMemset(c->trunc + (size_t)traj0 * nb, 0, sizeof(double) * n * nb));
+  const long long per_traj = (long long)c->L * c->slot;
+  const int chunk = 8;
+  double* stage = nullptr;
+  st = dalloc(c, &stage, 2 * (size_t)per_traj * chunk);
+  if (st != LT_OK) return st;
+  for (int t = 0; t < n && st == LT_OK; t += chunk) {
+    const int m = n - t < chunk ? n - t : chunk;
+    cudaError_t e = cudaMemcpy(stage, B + 2 * (size_t)per_traj * t, sizeof(double) * 2 * per_traj * m,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_convert_in(c, stage, per_traj * m, per_traj * (traj0 + t));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_set_state", cudaGetErrorString(e));
+  }
+  cudaFree(stage);
+  return st;
+}
+
+lt_status lt_get_state(lt_ctx c, int32_t traj0, int32_t n, int32_t* dims, double* lam, double* B) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (traj0 < 0 || n < 0 || traj0 + (long long)n > c->n_traj) return LT_ERR_ARG;
+  const size_t nb = c->L - 1;
+  LT_CK(cudaStreamSynchronize(c->stream));
+  if (dims) LT_CK(cudaMemcpy(dims, c->dims + (size_t)traj0 * nb, sizeof(int) * n * nb, cudaMemcpyDeviceToHost));
+  if (lam)
+    LT_CK(cudaMemcpy(lam, c->lam + (size_t)traj0 * nb * c->chi, sizeof(double) * n * nb * c->chi,
+                     cudaMemcpyDeviceToHost));
+  if (!B) return LT_OK;
+  const long long per_traj = (long long)c->L * c->slot;
+  const int chunk = 8;
+  double* stage = nullptr;
+  st = dalloc(c, &stage, 2 * (size_t)per_traj * chunk);
+  if (st != LT_OK) return st;
+  for (int t = 0; t < n && st == LT_OK; t += chunk) {
+    const int m = n - t < chunk ? n - t : chunk;
+    cudaError_t e = launch_convert_out(c, stage, per_traj * m, per_traj * (traj0 + t));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(B + 2 * (size_t)per_traj * t, stage, sizeof(double) * 2 * per_traj * m,
+                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_get_state", cudaGetErrorString(e));
+  }
+  cudaFree(stage);
+  return st;
+}
+
+// checkpoint file: magic, header ints, step, then dims, lam, trunc and the raw
+// site tensors in the context's precision
+lt_status lt_save(lt_ctx c, const char* path) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (!path) return LT_ERR_ARG;
+  const size_t nb = c->L - 1, nt = c->n_traj;
+  std::vector<int> dims(nt * nb);
+  std::vector<double> lam(nt * nb * c->chi), tr(nt * nb);
+  std::vector<char> B(nt * c->L * c->slot * c->celt);
+  LT_CK(cudaStreamSynchronize(c->stream));
+  LT_CK(cudaMemcpy(dims.data(), c->dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  LT_CK(cudaMemcpy(lam.data(), c->lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  LT_CK(cudaMemcpy(tr.data(), c->trunc, tr.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  LT_CK(cudaMemcpy(B.data(), c->B, B.size(), cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, LT_ERR_ARG, "lt_save", "cannot open file");
+  const char magic[8] = {'L', 'T', 'C', 'K', 'P', 'T', '0', '1'};
+  const int hdr[4] = {c->L, c->chi, c->n_traj, c->prec};
+  const long long stepc = c->step_counter;
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 4, f) == 4 &&
+            std::fwrite(&stepc, sizeof(stepc), 1, f) == 1 &&
+            std::fwrite(dims.data(), sizeof(int), dims.size(), f) == dims.size() &&
+            std::fwrite(lam.data(), sizeof(double), lam.size(), f) == lam.size() &&
+            std::fwrite(tr.data(), sizeof(double), tr.size(), f) == tr.size() &&
+            std::fwrite(B.data(), 1, B.size(), f) == B.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? LT_OK : fail(c, LT_ERR_ARG, "lt_save", "short write");
+}
+
+lt_status lt_load(lt_ctx c, const char* path) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (!path) return LT_ERR_ARG;
+  const size_t nb = c->L - 1, nt = c->n_traj;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, LT_ERR_ARG, "lt_load", "cannot open file");
+  char magic[8];
+  int hdr[4];
+  long long stepc = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "LTCKPT01", 8) == 0 &&
+            std::fread(hdr, sizeof(int), 4, f) == 4 && hdr[0] == c->L && hdr[1] == c->chi &&
+            hdr[2] == c->n_traj && hdr[3] == c->prec && std::fread(&stepc, sizeof(stepc), 1, f) == 1;
+  std::vector<int> dims(nt * nb);
+  std::vector<double> lam(nt * nb * c->chi), tr(nt * nb);
+  std::vector<char> B(nt * c->L * c->slot * c->celt);
+  ok = ok && std::fread(dims.data(), sizeof(int), dims.size(), f) == dims.size() &&
+       std::fread(lam.data(), sizeof(double), lam.size(), f) == lam.size() &&
+       std::fread(tr.data(), sizeof(double), tr.size(), f) == tr.size() &&
+       std::fread(B.data(), 1, B.size(), f) == B.size();
+  std::fclose(f);
+  if (!ok) return fail(c, LT_ERR_ARG, "lt_load", "checkpoint does not match this context");
+  for (int d : dims)
+    if (d < 1 || d > c->chi) return fail(c, LT_ERR_ARG, "lt_load", "bond dimension out of range");
+  LT_CK(cudaStreamSynchronize(c->stream));
+  LT_CK(cudaMemcpy(c->dims, dims.data(), dims.size() * sizeof(int), cudaMemcpyHostToDevice));
+  LT_CK(cudaMemcpy(c->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
+  LT_CK(cudaMemcpy(c->trunc, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice));
+  LT_CK(cudaMemcpy(c->B, B.data(), B.size(), cudaMemcpyHostToDevice));
+  c->step_counter = stepc;
+  return LT_OK;
+}
+
+}  // extern "C"

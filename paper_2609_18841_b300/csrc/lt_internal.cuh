@@ -1,0 +1,211 @@
+// Internal declarations of the lindtebd CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lindtebd.h"
+
+#define LT_MAX_CHI 64
+#define LT_MAX_DIM (2 * LT_MAX_CHI)  // largest theta side, d * chi_max
+#define LT_BLOCK 256
+
+// device error bits (ctx->err_dev)
+#define LT_EBIT_THETA_ZERO 1   // a theta matrix vanished
+#define LT_EBIT_PROB 2         // jump probability per step >= 0.5
+#define LT_EBIT_NOCONV 4       // Jacobi hit its sweep limit (recorded, not fatal)
+#define LT_EBIT_BADARG 8       // replayed channel out of range
+
+// ---- complex arithmetic on float2 / double2 ------------------------------------
+template <typename R> struct CT;
+template <> struct CT<float> { typedef float2 T; };
+template <> struct CT<double> { typedef double2 T; };
+
+template <typename T> __host__ __device__ __forceinline__ T cmk(double x, double y) {
+  T r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T> __device__ __forceinline__ T czero() {
+  T r;
+  r.x = 0;
+  r.y = 0;
+  return r;
+}
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cfma(T& acc, const T a, const T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+template <typename T> __device__ __forceinline__ void cfmac(T& acc, const T a, const T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.y, b.x, acc.y);
+  acc.y = fma(-a.x, b.y, acc.y);
+}
+template <typename T> __device__ __forceinline__ T cmul(const T a, const T b) {
+  T r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename T, typename R> __device__ __forceinline__ T cscale(const T a, R s) {
+  T r;
+  r.x = a.x * s;
+  r.y = a.y * s;
+  return r;
+}
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) ---------------------------------------
+__device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_t& x2,
+                                             uint32_t& x3, uint32_t k0, uint32_t k1) {
+  const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(m0, x0), lo0 = m0 * x0;
+  uint32_t hi1 = __umulhi(m1, x2), lo1 = m1 * x2;
+  uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+  x0 = y0;
+  x1 = lo1;
+  x2 = y2;
+  x3 = lo0;
+}
+// uniform double in [0,1) for counter (c0, step, purpose, step >> 32) and key seed
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint32_t c0, uint64_t step,
+                                                 uint32_t purpose) {
+  uint32_t x0 = c0, x1 = (uint32_t)step, x2 = purpose, x3 = (uint32_t)(step >> 32);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    philox_round(x0, x1, x2, x3, k0, k1);
+  }
+  return ((double)(x0 >> 5) * 67108864.0 + (double)(x1 >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// ---- launch descriptors -----------------------------------------------------------
+// One launch of the two-site update over a list of trajectories and a set of
+// bonds bond0, bond0 + 2, ..., bond0 + 2 (nb - 1).
+template <typename R> struct BondArgs {
+  typedef typename CT<R>::T Tc;
+  Tc* B;            // [n_traj][L][slot]
+  double* lam;      // [n_traj][L-1][chi]
+  int* dims;        // [n_traj][L-1]
+  double* trunc;    // [n_traj][L-1]
+  const int* trajs; // trajectory list
+  const int* n_trajs;
+  int bond0, nb;
+  const double2* gates;  // [L-1][16] or nullptr = identity
+  const int* channel;    // per-trajectory channel, used when rl_filter
+  int rl_filter;         // 1: apply only if bond0 <= site(channel) - 1
+  int L, chi, slot;
+  double cut;
+  int* err;
+  Tc* scratch;           // per-CTA workspace when it does not fit shared memory
+  long long scratch_stride;
+  int use_smem;
+  int max_sweeps;
+  double tol;            // Jacobi threshold, 0 = 4 eps sqrt(n)
+  int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
+};
+
+struct EnvArgs {
+  void* B;
+  const double* lam;
+  const int* dims;
+  int L, chi, slot, n_traj;
+  void* scratch;  // per-CTA environment workspace
+  long long scratch_stride;
+  double* density;      // [n_traj][L]
+  double* rates;        // [n_traj][3L]
+  const double* gl;     // [L]
+  const double* gg;
+  const double* gd;
+  double dt;
+  int decide;           // 1: draw/replay the jump decision
+  const int* replay;    // [n_traj] or nullptr
+  int* channel;         // [n_traj]
+  int* evolve;          // [n_traj]
+  uint64_t seed;
+  long long traj_offset;
+  long long step;
+  int* err;
+  double2* corr;        // [n_traj][L][L] for the correlation kernel
+};
+
+// ---- context -------------------------------------------------------------------------
+struct lt_ctx_s {
+  int L, chi, n_traj, prec, order, fermionic, max_sweeps;
+  double J, dt, cut, jacobi_tol;
+  uint64_t seed;
+  long long traj_offset;
+  std::vector<double> gl, gg, gd;
+  std::vector<uint8_t> occ;
+  int init;
+
+  cudaStream_t stream;
+  bool own_stream;
+  int device, num_sms;
+
+  int slot;         // complex elements per site tensor slot = 2 chi^2
+  size_t celt;      // bytes per complex element (8 mixed, 16 fp64)
+  void* B;          // site tensors
+  double* lam;
+  int* dims;
+  double* trunc;
+  int* evolve;
+  int* channel;
+  int* replay;
+  int* active_list;
+  int* jumped_list;
+  int* counts;      // [0] = n_active, [1] = n_jumped
+  double* density;
+  double* rates;
+  double* gam;      // [3][L]
+  int* err_dev;
+  int* sweep_hist;  // [64]
+
+  // gate cache: up to 8 distinct tau values
+  std::vector<double> gate_taus;
+  double2* gates;   // [8][L-1][16]
+
+  void* bond_scratch;
+  long long bond_scratch_stride;
+  int bond_grid, bond_use_smem;
+  size_t bond_smem;
+
+  void* env_scratch;
+  long long env_scratch_stride;
+  int env_grid;
+
+  double2* corr;    // [n_traj][L][L], allocated on first correlation measurement
+  double* red;      // reduction output buffer
+
+  long long step_counter;
+  long long launches;
+  bool poisoned;
+  std::string last_error;
+};
+
+// ---- kernel launchers (lt_kernels.cu) ----------------------------------------------
+cudaError_t launch_bond(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0, int nb,
+                        const double2* gates, int rl_filter);
+cudaError_t launch_env(lt_ctx_s* c, int decide, long long step, const int* replay);
+cudaError_t launch_jump_apply(lt_ctx_s* c);
+cudaError_t launch_compact(lt_ctx_s* c);
+cudaError_t launch_corr(lt_ctx_s* c);
+cudaError_t launch_reduce_density(lt_ctx_s* c, double* out_mean, double* out_sem);
+cudaError_t launch_reduce_corr(lt_ctx_s* c, double* out);
+cudaError_t launch_convert_in(lt_ctx_s* c, const double* src, long long n, long long dst_off);
+cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long src_off);
+cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev);
+size_t bond_smem_bytes(int chi, size_t celt);
+size_t env_scratch_elems(int L, int chi);

@@ -1,0 +1,298 @@
+"""ctypes binding of the lindtebd C ABI (include/lindtebd.h).
+
+Argument marshalling only: every step of the integrator runs in the CUDA
+library.  Importing this module loads liblindtebd.so and raises ImportError if
+it has not been built (there is no fallback implementation).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblindtebd.so")
+
+LT_OK, LT_ERR_ARG, LT_ERR_OOM, LT_ERR_CUDA, LT_ERR_NUMERICAL, LT_ERR_TIMEOUT, \
+    LT_ERR_STATE, LT_ERR_UNSUPPORTED = range(8)
+LT_TRAJ, LT_QSD, LT_MPDO, LT_PURIFIED = range(4)
+LT_FP64, LT_MIXED = 0, 1
+LT_INIT_VACUUM, LT_INIT_NEEL, LT_INIT_DOMAIN_WALL, LT_INIT_PRODUCT = range(4)
+INIT_NAMES = {"vacuum": LT_INIT_VACUUM, "neel": LT_INIT_NEEL,
+              "domain_wall": LT_INIT_DOMAIN_WALL, "product": LT_INIT_PRODUCT}
+
+
+class lt_config(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int32), ("chi_max", ctypes.c_int32), ("n_traj", ctypes.c_int32),
+        ("kraus_dim", ctypes.c_int32), ("method", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("init", ctypes.c_int32),
+        ("trotter_order", ctypes.c_int32), ("product_occ", ctypes.c_void_p),
+        ("J", ctypes.c_double), ("dt", ctypes.c_double),
+        ("gamma_loss", ctypes.c_void_p), ("gamma_gain", ctypes.c_void_p),
+        ("gamma_deph", ctypes.c_void_p), ("fermionic_jumps", ctypes.c_int32),
+        ("max_sweeps", ctypes.c_int32), ("svd_cut", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("traj_offset", ctypes.c_int64),
+        ("jacobi_tol", ctypes.c_double),
+    ]
+
+
+EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
+           "lt_step", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
+           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_launch_count", "lt_stream", "lt_get_step",
+           "lt_status_str", "lt_last_error"]
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("liblindtebd.so is not built (run paper_2609_18841_b300/build.py)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "lt_create": ([ctypes.POINTER(lt_config), P, ctypes.POINTER(P)], I32),
+        "lt_destroy": ([P], I32),
+        "lt_apply_layer": ([P, I32, D], I32),
+        "lt_apply_jumps": ([P, I64, P, P], I32),
+        "lt_apply_noise": ([P, I64], I32),
+        "lt_step": ([P, I32], I32),
+        "lt_measure_density": ([P, P, P, P], I32),
+        "lt_measure_corr": ([P, P, P, P, P], I32),
+        "lt_get_stats": ([P, P, P], I32),
+        "lt_set_state": ([P, I32, I32, P, P, P], I32),
+        "lt_get_state": ([P, I32, I32, P, P, P], I32),
+        "lt_save": ([P, ctypes.c_char_p], I32),
+        "lt_load": ([P, ctypes.c_char_p], I32),
+        "lt_get_sweep_histogram": ([P, P, I32], I32),
+        "lt_launch_count": ([P], I64),
+        "lt_stream": ([P], P),
+        "lt_get_step": ([P], I64),
+        "lt_status_str": ([I32], ctypes.c_char_p),
+        "lt_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = load_library()
+
+
+class LtError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = "%s failed: %s" % (where, _lib.lt_status_str(status).decode())
+        if detail:
+            msg += " (%s)" % detail
+        super().__init__(msg)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(status, where, ctx=None):
+    if status != LT_OK:
+        detail = _lib.lt_last_error(ctx).decode() if ctx else ""
+        raise LtError(status, where, detail)
+
+
+def _arr(x, L, dtype=np.float64):
+    if x is None:
+        return None
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype), (L,)))
+
+
+def lt_create(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.05,
+              trotter_order=2, gamma_loss=None, gamma_gain=None, gamma_deph=None,
+              fermionic_jumps=1, svd_cut=1e-12, seed=0, traj_offset=0, product_occ=None,
+              method=LT_TRAJ, stream=None, max_sweeps=0, jacobi_tol=0.0):
+    """Create a context; returns (handle, keepalive) -- keep both until lt_destroy."""
+    cfg = lt_config()
+    cfg.L, cfg.chi_max, cfg.n_traj = L, chi_max, n_traj
+    cfg.kraus_dim, cfg.method, cfg.precision = 0, method, precision
+    cfg.init = INIT_NAMES[init] if isinstance(init, str) else int(init)
+    cfg.trotter_order, cfg.J, cfg.dt = trotter_order, J, dt
+    keep = [_arr(gamma_loss, L), _arr(gamma_gain, L), _arr(gamma_deph, L),
+            None if product_occ is None else np.ascontiguousarray(product_occ, np.uint8)]
+    cfg.gamma_loss, cfg.gamma_gain, cfg.gamma_deph = (_ptr(k) for k in keep[:3])
+    cfg.product_occ = _ptr(keep[3])
+    cfg.fermionic_jumps, cfg.svd_cut = int(fermionic_jumps), svd_cut
+    cfg.seed, cfg.traj_offset = seed, traj_offset
+    cfg.max_sweeps, cfg.jacobi_tol = max_sweeps, jacobi_tol
+    h = ctypes.c_void_p()
+    _check(_lib.lt_create(ctypes.byref(cfg), stream, ctypes.byref(h)), "lt_create")
+    return h
+
+
+def lt_destroy(ctx):
+    _check(_lib.lt_destroy(ctx), "lt_destroy")
+
+
+def lt_apply_layer(ctx, parity, tau):
+    _check(_lib.lt_apply_layer(ctx, parity, tau), "lt_apply_layer", ctx)
+
+
+def lt_apply_jumps(ctx, step, replay=None, n_traj=None, want_channels=False):
+    rep = None if replay is None else np.ascontiguousarray(replay, np.int32)
+    out = None
+    if want_channels:
+        out = np.empty(n_traj if n_traj is not None else len(rep), np.int32)
+    _check(_lib.lt_apply_jumps(ctx, step, _ptr(rep), _ptr(out)), "lt_apply_jumps", ctx)
+    return out
+
+
+def lt_apply_noise(ctx, step):
+    _check(_lib.lt_apply_noise(ctx, step), "lt_apply_noise", ctx)
+
+
+def lt_step(ctx, n_steps):
+    _check(_lib.lt_step(ctx, n_steps), "lt_step", ctx)
+
+
+def lt_measure_density(ctx, L, n_traj, per_traj=False, out=None):
+    mean = np.empty(L) if out is None else out[0]
+    sem = np.empty(L) if out is None else out[1]
+    pt = np.empty((n_traj, L)) if per_traj else None
+    _check(_lib.lt_measure_density(ctx, _ptr(mean), _ptr(sem), _ptr(pt)), "lt_measure_density", ctx)
+    return mean, sem, pt
+
+
+def lt_measure_corr(ctx, L, n_traj, per_traj=False):
+    re, im = np.empty((L, L)), np.empty((L, L))
+    pre = np.empty((n_traj, L, L)) if per_traj else None
+    pim = np.empty((n_traj, L, L)) if per_traj else None
+    _check(_lib.lt_measure_corr(ctx, _ptr(re), _ptr(im), _ptr(pre), _ptr(pim)),
+           "lt_measure_corr", ctx)
+    return re + 1j * im, (None if pre is None else pre + 1j * pim)
+
+
+def lt_get_stats(ctx, L, n_traj):
+    tw = np.empty(n_traj)
+    dims = np.empty((n_traj, L - 1), np.int32)
+    _check(_lib.lt_get_stats(ctx, _ptr(tw), _ptr(dims)), "lt_get_stats", ctx)
+    return tw, dims
+
+
+def lt_set_state(ctx, traj0, dims, lam, B):
+    """dims [n, L-1] int32, lam [n, L-1, chi] float64, B [n, L, 2 chi^2] complex128."""
+    dims = np.ascontiguousarray(dims, np.int32)
+    lam = np.ascontiguousarray(lam, np.float64)
+    B = np.ascontiguousarray(B, np.complex128)
+    _check(_lib.lt_set_state(ctx, traj0, dims.shape[0], _ptr(dims), _ptr(lam), _ptr(B)),
+           "lt_set_state", ctx)
+
+
+def lt_get_state(ctx, traj0, n, L, chi):
+    dims = np.empty((n, L - 1), np.int32)
+    lam = np.empty((n, L - 1, chi))
+    B = np.empty((n, L, 2 * chi * chi), np.complex128)
+    _check(_lib.lt_get_state(ctx, traj0, n, _ptr(dims), _ptr(lam), _ptr(B)), "lt_get_state", ctx)
+    return dims, lam, B
+
+
+def lt_save(ctx, path):
+    _check(_lib.lt_save(ctx, path.encode()), "lt_save", ctx)
+
+
+def lt_load(ctx, path):
+    _check(_lib.lt_load(ctx, path.encode()), "lt_load", ctx)
+
+
+def lt_get_sweep_histogram(ctx, clear=False):
+    h = np.zeros(64, np.int32)
+    _check(_lib.lt_get_sweep_histogram(ctx, _ptr(h), int(clear)), "lt_get_sweep_histogram", ctx)
+    return h
+
+
+def lt_launch_count(ctx):
+    return int(_lib.lt_launch_count(ctx))
+
+
+def lt_stream(ctx):
+    return _lib.lt_stream(ctx)
+
+
+def lt_get_step(ctx):
+    return int(_lib.lt_get_step(ctx))
+
+
+# ---- packing helpers: list-of-tensors MPS <-> the library's padded layout ---------------
+def pack_state(mps_list, L, chi):
+    """mps_list: per trajectory (B list of (chi_l, 2, chi_r), lam list, dims)."""
+    n = len(mps_list)
+    dims = np.zeros((n, L - 1), np.int32)
+    lam = np.zeros((n, L - 1, chi))
+    Bp = np.zeros((n, L, 2 * chi * chi), np.complex128)
+    for t, (B, lm, dm) in enumerate(mps_list):
+        dims[t] = dm
+        for b in range(L - 1):
+            lam[t, b, :len(lm[b])] = lm[b]
+        for i in range(L):
+            flat = np.asarray(B[i]).reshape(-1)
+            Bp[t, i, :flat.size] = flat
+    return dims, lam, Bp
+
+
+def unpack_state(dims, lam, Bp, L):
+    """Inverse of pack_state for one trajectory."""
+    full = [1] + [int(x) for x in dims] + [1]
+    B = [Bp[i, :full[i] * 2 * full[i + 1]].reshape(full[i], 2, full[i + 1]) for i in range(L)]
+    lm = [lam[b, :full[b + 1]] for b in range(L - 1)]
+    return B, lm
+
+
+class Ensemble:
+    """Owner of one context: holds the handle and its sizes."""
+
+    def __init__(self, L, chi_max, n_traj, **kw):
+        self.L, self.chi, self.n_traj = L, chi_max, n_traj
+        self.ctx = lt_create(L, chi_max, n_traj, **kw)
+
+    def close(self):
+        if self.ctx is not None:
+            lt_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lt_step(self.ctx, n)
+
+    def apply_jumps(self, step, replay=None, want_channels=True):
+        return lt_apply_jumps(self.ctx, step, replay, self.n_traj, want_channels)
+
+    def apply_layer(self, parity, tau):
+        lt_apply_layer(self.ctx, parity, tau)
+
+    def density(self, per_traj=False):
+        return lt_measure_density(self.ctx, self.L, self.n_traj, per_traj)
+
+    def corr(self, per_traj=False):
+        return lt_measure_corr(self.ctx, self.L, self.n_traj, per_traj)
+
+    def stats(self):
+        return lt_get_stats(self.ctx, self.L, self.n_traj)
+
+    def set_state(self, traj0, mps_list):
+        dims, lam, B = pack_state(mps_list, self.L, self.chi)
+        lt_set_state(self.ctx, traj0, dims, lam, B)
+
+    def get_state(self, traj0, n):
+        return lt_get_state(self.ctx, traj0, n, self.L, self.chi)
+
+    def launches(self):
+        return lt_launch_count(self.ctx)
+
+    def sweep_histogram(self, clear=False):
+        return lt_get_sweep_histogram(self.ctx, clear)

@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  FP64 mode must agree per trajectory within 1e-10 (scaled
+by the largest |value|); decisions drawn from Philox on both sides must agree
+exactly; mixed mode is held to the per-observable bounds stated below."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import tebd
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+def _lt():
+    from paper_2609_18841_b300 import lindtebd
+    return lindtebd
+
+
+def oracle_cfg(w, L=None, chi=None, cut=1e-12, **over):
+    L = L or w["L"]
+    d = dict(J=w["J"], dt=w["dt"], chi_max=chi or w["chi_max"], svd_cut=cut,
+             gamma_loss=w["gamma_loss"], gamma_gain=w["gamma_gain"],
+             gamma_deph=w["gamma_deph"], fermionic=bool(w["fermionic"]),
+             trotter_order=w["trotter_order"], occupation=workloads.occupation(L, w["init"]),
+             seed=w["seed"])
+    d.update(over)
+    return tebd.TrajectoryConfig(L, **d)
+
+
+def gpu_ensemble(cfg, n_traj, precision, init="neel"):
+    lt = _lt()
+    return lt.Ensemble(cfg.L, cfg.chi_max, n_traj, precision=precision, init=init, J=cfg.J,
+                       dt=cfg.dt, trotter_order=cfg.trotter_order, gamma_loss=cfg.gamma_loss,
+                       gamma_gain=cfg.gamma_gain, gamma_deph=cfg.gamma_deph,
+                       fermionic_jumps=int(cfg.fermionic), svd_cut=cfg.svd_cut, seed=cfg.seed)
+
+
+def gpu_steps(ens, cfg, n_steps, replay=None, step0=0):
+    chans = []
+    for s in range(n_steps):
+        rep = None if replay is None else np.ascontiguousarray(replay[:, s], np.int32)
+        chans.append(ens.apply_jumps(step0 + s, rep))
+        for parity, tau in cfg.layers():
+            ens.apply_layer(parity, tau)
+    return np.stack(chans, axis=1)
+
+
+def assert_close(got, want, tol, what):
+    scale = max(1.0, float(np.abs(want).max()))
+    err = float(np.abs(got - want).max())
+    assert err <= tol * scale, "%s: max |diff| %.3e > %.1e" % (what, err, tol * scale)
+    return err
+
+
+# ---- W1: L=8, chi=16, fermionic loss 0.1, Neel, dt=0.05, 40 steps ----------------------
+@pytest.fixture(scope="module")
+def w1_oracle():
+    cfg = oracle_cfg(workloads.W1)
+    n = 24
+    res = tebd.run_trajectories(cfg, workloads.W1["n_steps"], list(range(n)), measure_corr=True)
+    return cfg, n, res
+
+
+def test_w1_fp64_sampled_decisions_and_observables(w1_oracle):
+    cfg, n, res = w1_oracle
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as ens:
+        chans = gpu_steps(ens, cfg, workloads.W1["n_steps"])
+        assert np.array_equal(chans, res["jumps"])
+        mean, sem, dens = ens.density(per_traj=True)
+        C, Cp = ens.corr(per_traj=True)
+        tw, dims = ens.stats()
+    assert_close(dens, res["density"], FP64_TOL, "density")
+    assert_close(Cp, res["corr"], FP64_TOL, "corr")
+    assert np.abs(mean - res["density"].mean(0)).max() < FP64_TOL
+    assert np.array_equal(dims, res["bond_dims"])
+    assert np.abs(tw - res["trunc"]).max() < 1e-12
+
+
+def test_w1_fp64_replay(w1_oracle):
+    cfg, n, res = w1_oracle
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as ens:
+        chans = gpu_steps(ens, cfg, workloads.W1["n_steps"], replay=res["jumps"])
+        assert np.array_equal(chans, res["jumps"])
+        _, _, dens = ens.density(per_traj=True)
+    assert_close(dens, res["density"], FP64_TOL, "density")
+
+
+def test_w1_mixed_replay_error_bounds(w1_oracle):
+    # mixed: single-precision tensors and rotations, double-precision singular
+    # values, norms and rates.  Per-trajectory bound 2e-5, ensemble mean 2e-6.
+    cfg, n, res = w1_oracle
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_MIXED) as ens:
+        gpu_steps(ens, cfg, workloads.W1["n_steps"], replay=res["jumps"])
+        mean, _, dens = ens.density(per_traj=True)
+        C, Cp = ens.corr(per_traj=True)
+    e1 = assert_close(dens, res["density"], 2e-5, "mixed density per trajectory")
+    e2 = assert_close(Cp, res["corr"], 2e-5, "mixed corr per trajectory")
+    e3 = assert_close(mean, res["density"].mean(0), 2e-6, "mixed density ensemble")
+    e4 = assert_close(C, res["corr"].mean(0), 2e-6, "mixed corr ensemble")
+    print("mixed errors: dens %.2e corr %.2e mean %.2e Cmean %.2e" % (e1, e2, e3, e4))
+
+
+# ---- synthetic states: ragged dims, several tiles, truncation active ---------------------
+@pytest.mark.parametrize("L,chi,ragged,seed", [(10, 8, True, 1), (12, 16, True, 2),
+                                               (9, 5, False, 3), (16, 32, True, 4)])
+def test_synthetic_state_one_step_fp64(L, chi, ragged, seed):
+    w = dict(workloads.W3, L=L, chi_max=chi, gamma_loss=0.3, gamma_gain=0.05, gamma_deph=0.1)
+    cfg = oracle_cfg(w, L=L, chi=chi, dt=0.05, seed=seed)
+    n = 3
+    states = [workloads.synthetic_mps(L, chi, seed=100 * seed + t, ragged=ragged) for t in range(n)]
+    res = tebd.run_trajectories(cfg, 2, list(range(n)), measure_corr=True,
+                                initial=[(B, lam) for B, lam, _ in states])
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as ens:
+        ens.set_state(0, states)
+        chans = gpu_steps(ens, cfg, 2)
+        _, _, dens = ens.density(per_traj=True)
+        _, Cp = ens.corr(per_traj=True)
+        tw, dims = ens.stats()
+    assert np.array_equal(chans, res["jumps"])
+    assert np.array_equal(dims, res["bond_dims"])
+    assert_close(dens, res["density"], FP64_TOL, "density")
+    assert_close(Cp, res["corr"], FP64_TOL, "corr")
+    assert np.abs(tw - res["trunc"]).max() < 1e-11
+
+
+def test_forced_jump_then_recanonicalise_fp64():
+    L, chi = 12, 16
+    cfg = oracle_cfg(dict(workloads.W3, gamma_gain=0.1, gamma_deph=0.1), L=L, chi=chi, dt=0.05)
+    n = 6
+    states = [workloads.synthetic_mps(L, chi, seed=70 + t, ragged=True) for t in range(n)]
+    # every channel kind at several sites, including both chain ends
+    replay = np.array([[0], [3 * 5 + 1], [3 * 11 + 0], [3 * 7 + 2], [3 * 11 + 1], [-1]])
+    res = tebd.run_trajectories(cfg, 1, list(range(n)), replay=replay, measure_corr=True,
+                                initial=[(B, lam) for B, lam, _ in states])
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as ens:
+        ens.set_state(0, states)
+        gpu_steps(ens, cfg, 1, replay=replay)
+        _, _, dens = ens.density(per_traj=True)
+        _, Cp = ens.corr(per_traj=True)
+        tw, dims = ens.stats()
+    assert np.array_equal(dims, res["bond_dims"])
+    assert_close(dens, res["density"], FP64_TOL, "density")
+    assert_close(Cp, res["corr"], FP64_TOL, "corr")
+
+
+# ---- the W3 chain at full size (L=64, chi_max=64) on sampled outputs -------------------
+def test_w3_full_size_sampled_trajectories_fp64_and_mixed():
+    L, chi, n = 64, 64, 2
+    cfg = oracle_cfg(workloads.W3)
+    states = [workloads.synthetic_mps(L, chi, seed=900 + t) for t in range(n)]
+    res = tebd.run_trajectories(cfg, 1, list(range(n)),
+                                initial=[(B, lam) for B, lam, _ in states])
+    lt = _lt()
+    for prec, tol in ((lt.LT_FP64, FP64_TOL), (lt.LT_MIXED, 2e-5)):
+        with gpu_ensemble(cfg, n, prec) as ens:
+            ens.set_state(0, states)
+            chans = gpu_steps(ens, cfg, 1, replay=res["jumps"])
+            _, _, dens = ens.density(per_traj=True)
+            _, dims = ens.stats()
+        assert np.array_equal(chans, res["jumps"])
+        if prec == lt.LT_FP64:
+            assert np.array_equal(dims, res["bond_dims"])
+        assert_close(dens, res["density"], tol, "density %d" % prec)
+
+
+# ---- edge cases --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,chi,init", [(2, 1, "neel"), (2, 2, "domain_wall"), (3, 1, "neel"),
+                                        (5, 2, "vacuum"), (7, 64, "neel")])
+def test_edge_cases_fp64(L, chi, init):
+    w = dict(workloads.W1, L=L, chi_max=chi, gamma_gain=0.2, init=init)
+    cfg = oracle_cfg(w, L=L, chi=chi)
+    n, steps = 5, 12
+    res = tebd.run_trajectories(cfg, steps, list(range(n)), measure_corr=True)
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_FP64, init=init) as ens:
+        chans = gpu_steps(ens, cfg, steps)
+        _, _, dens = ens.density(per_traj=True)
+        _, Cp = ens.corr(per_traj=True)
+    assert np.array_equal(chans, res["jumps"])
+    assert_close(dens, res["density"], FP64_TOL, "density")
+    assert_close(Cp, res["corr"], FP64_TOL, "corr")
+
+
+def test_lt_step_matches_manual_schedule_and_checkpoint(tmp_path):
+    cfg = oracle_cfg(workloads.W1, L=10, chi=8)
+    lt = _lt()
+    n = 16
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as a:
+        a.step(10)
+        da = a.density(per_traj=True)[2]
+        assert lt.lt_get_step(a.ctx) == 10
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as b:
+        b.step(4)
+        lt.lt_save(b.ctx, str(tmp_path / "ck.bin"))
+    with gpu_ensemble(cfg, n, lt.LT_FP64) as c:
+        lt.lt_load(c.ctx, str(tmp_path / "ck.bin"))
+        assert lt.lt_get_step(c.ctx) == 4
+        c.step(6)
+        dc = c.density(per_traj=True)[2]
+    assert np.array_equal(da, dc)
+    res = tebd.run_trajectories(cfg, 10, list(range(n)))
+    assert_close(da, res["density"], FP64_TOL, "lt_step density")
+
+
+def test_large_dt_is_reported_and_poisons_the_context():
+    lt = _lt()
+    ens = lt.Ensemble(6, 4, 2, precision=lt.LT_FP64, dt=2.0, gamma_loss=1.0)
+    with pytest.raises(lt.LtError) as e:
+        ens.apply_jumps(0)
+    assert e.value.status == lt.LT_ERR_NUMERICAL
+    with pytest.raises(lt.LtError) as e:
+        ens.step(1)
+    assert e.value.status == lt.LT_ERR_STATE
+    ens.close()
