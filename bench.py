@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: two-site TEBD updates/s of the batched quantum-trajectory
+integrator on the W3 chain (L=64, chi_max=64, 4096 trajectories, fermionic
+loss 0.2 on every site, dt=0.02), started from a synthetic MPS at the bond
+dimensions chi_max allows (ragged only where the chain ends cap them).
+
+A step is one full time step of every trajectory: jump rates from exact
+environments, the Philox jump-or-evolve decision, jumps with the canonical-form
+sweep, and the three Trotter layers A(dt/2) B(dt) A(dt/2) of the two-site
+update.  The state (17 GB of complex64 site tensors) is far larger than L2, so
+no flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = ("two-site TEBD updates/s (L=64, χ=64, 4096 traj) mixed vs FP64 at 1e-6; "
+          "p50/p99 latency")
+UNIT = "updates/s"
+POOL = 16            # distinct synthetic histories, repeated across the ensemble
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--traj", type=int, default=workloads.W3["n_traj"])
+    ap.add_argument("--fp64-traj", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def w3_kwargs(precision_name):
+    w = workloads.W3
+    return dict(J=w["J"], dt=w["dt"], trotter_order=w["trotter_order"],
+                gamma_loss=w["gamma_loss"], gamma_gain=w["gamma_gain"],
+                gamma_deph=w["gamma_deph"], fermionic_jumps=w["fermionic"],
+                svd_cut=1e-12 if precision_name == "fp64" else 1e-6, seed=w["seed"])
+
+
+def state_pool(L, chi, n_pool, seed=1234):
+    from paper_2609_18841_b300 import lindtebd as lt
+    mps = []
+    for t in range(n_pool):
+        B, lam, dims = workloads.synthetic_mps(L, chi, seed=seed + t)
+        mps.append((B, lam, dims))
+    return mps, lt.pack_state(mps, L, chi)
+
+
+def upload(lt, ctx, packed, n_traj, pinned=None):
+    dims, lam, B = packed if pinned is None else pinned
+    n_pool = dims.shape[0]
+    for t0 in range(0, n_traj, n_pool):
+        m = min(n_pool, n_traj - t0)
+        lt.lt_set_state(ctx, t0, dims[:m], lam[:m], B[:m])
+    return n_traj // n_pool * B[:n_pool].nbytes + B[:n_traj % n_pool].nbytes
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def cpu_baseline(seconds, L=64, chi=64, tag="cpu_baseline"):
+    """The FP64 oracle as it stands on the host cores: whole time steps of single
+    trajectories of the same workload, until about `seconds` of CPU work."""
+    from oracle import tebd
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    w = workloads.W3
+    cfg = tebd.TrajectoryConfig(L, J=w["J"], dt=w["dt"], chi_max=chi, svd_cut=1e-12,
+                                gamma_loss=w["gamma_loss"], seed=w["seed"],
+                                occupation=workloads.occupation(L, "neel"))
+    gates = tebd.StepGates(cfg)
+    updates = 0
+    n_traj = 0
+    t0 = time.perf_counter()
+    while True:
+        B, lam, _ = workloads.synthetic_mps(L, chi, seed=1234 + n_traj % POOL)
+        tr = tebd.Trajectory.from_tensors(cfg, B, lam)
+        ch = tebd.step_trajectory(tr, gates, n_traj, 0)
+        if ch >= 0:
+            site = ch // 3
+            updates += max(site - 1, 0) + (L - 1)
+        else:
+            updates += sum(len(range(p, L - 1, 2)) for p, _ in cfg.layers())
+        n_traj += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": updates / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": "%d W3 trajectories x 1 time step from synthetic chi=64 states "
+                      "(%d two-site updates, %.1f s)" % (n_traj, updates, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    per_step = max(1.0, 25.0 / max(K + W, 1))
+    vals = []
+    for i in range(W + K):
+        r = cpu_baseline(per_step)
+        if i >= W:
+            vals.append(r)
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": K, "warmup": W,
+            "ms_per_step": 1000.0 * per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "W3s: L=64, chi_max=64, fermionic loss 0.2, dt=0.02, "
+                                   "synthetic chi=64 states (oracle: sampled trajectories)",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": dict(vals[-1], value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def algorithmic_tflops(flops, seconds):
+    return flops / seconds / 1e12
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2609_18841_b300 import lindtebd as lt
+
+    L, chi, n_traj = workloads.W3["L"], workloads.W3["chi_max"], args.traj
+    dt = workloads.W3["dt"]
+    stream = torch.cuda.Stream()
+    mps, packed = state_pool(L, chi, POOL)
+    pk, src = peaks()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- headline: mixed precision ------------------------------------------------------
+    ens = lt.Ensemble(L, chi, n_traj, precision=lt.LT_MIXED, init="neel",
+                      traj_offset=rank * n_traj, stream=stream.cuda_stream, **w3_kwargs("mixed"))
+    upload(lt, ens.ctx, packed, n_traj)
+    layers = [(0, dt / 2), (1, dt), (0, dt / 2)]
+    step = 0
+
+    def one_step(record=None):
+        nonlocal step
+        lt.lt_apply_jumps(ens.ctx, step)
+        for parity, tau in layers:
+            if record is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lt.lt_apply_layer(ens.ctx, parity, tau)
+                b.record(stream)
+                record.append((a, b))
+            else:
+                lt.lt_apply_layer(ens.ctx, parity, tau)
+        step += 1
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    ens.counters(clear=True)
+    ens.sweep_histogram(clear=True)
+    launches0 = ens.launches()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(uuid)
+    layer_ev, step_ev = [], []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        one_step(layer_ev)
+        s1.record(stream)
+        step_ev.append((s0, s1))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    cnt = ens.counters()
+    hist = ens.sweep_histogram()
+    launches = ens.launches() - launches0
+    step_ms = sorted(a.elapsed_time(b) for a, b in step_ev)
+    layer_ms = [a.elapsed_time(b) for a, b in layer_ev]
+    updates = cnt["updates"]
+    if world > 1:
+        tu = torch.tensor([float(updates)], device="cuda")
+        torch.distributed.all_reduce(tu)
+        updates_all = float(tu.item())
+    else:
+        updates_all = float(updates)
+    value = updates_all / (total_ms / 1e3)
+    mean_layer_s = float(np.mean(layer_ms)) / 1e3
+    flops_per_layer = cnt["layer_flops"] / max(len(layer_ms), 1)
+    achieved = algorithmic_tflops(flops_per_layer, mean_layer_s)
+    alu_peak = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * FP32_LANES_PER_SM * 2 / 1e12
+    sweeps_mean = float(np.sum(np.arange(64) * hist) / max(hist.sum(), 1))
+    ens.close()
+    del ens
+    torch.cuda.synchronize()
+
+    # ---- plain FP64 path on a subset (same kernels in double precision) ----------------
+    fp64 = None
+    if args.fp64_traj > 0 and rank == 0:
+        n64 = args.fp64_traj
+        e64 = lt.Ensemble(L, chi, n64, precision=lt.LT_FP64, init="neel",
+                          stream=stream.cuda_stream, **w3_kwargs("fp64"))
+        upload(lt, e64.ctx, packed, n64)
+        lt.lt_step(e64.ctx, 1)
+        torch.cuda.synchronize()
+        e64.counters(clear=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lt.lt_step(e64.ctx, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        c64 = e64.counters()
+        fp64 = {"updates_per_s": c64["updates"] / (a.elapsed_time(b) / 1e3),
+                "n_traj": n64, "steps": 1}
+        e64.close()
+
+    # ---- end to end through the public API with host buffers ---------------------------
+    e2e = None
+    if not args.no_e2e:
+        dims, lam, B = packed
+        pinned = [torch.from_numpy(x).pin_memory().numpy() for x in (dims, lam, B)]
+        mean_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
+        sem_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e = lt.Ensemble(L, chi, n_traj, precision=lt.LT_MIXED, init="neel",
+                        traj_offset=rank * n_traj, stream=stream.cuda_stream,
+                        **w3_kwargs("mixed"))
+        h2d = upload(lt, e.ctx, None, n_traj, pinned=pinned)
+        for _ in range(args.steps):
+            lt.lt_step(e.ctx, 1)
+            lt.lt_measure_density(e.ctx, L, n_traj, out=(mean_h, sem_h))
+        ce = e.counters()
+        e.close()
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = t1 - t0
+        if world > 1:
+            tt = torch.tensor([e2e_s, float(ce["updates"])], device="cuda")
+            mx = tt.clone()
+            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(tt)
+            e2e_s, e2e_up = float(mx[0]), float(tt[1])
+        else:
+            e2e_up = float(ce["updates"])
+        e2e = {"value": e2e_up / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d // max(args.steps, 1)),
+               "d2h_bytes_per_step": int(2 * L * 8),
+               "includes": "lt_create, upload of the initial ensemble from pinned host "
+                           "memory, %d x (lt_step + lt_measure_density to host), lt_destroy"
+                           % args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "W3s: L=64, chi_max=64, %d trajectories per GPU, fermionic "
+                                   "loss 0.2 on every site, dt=0.02, 2nd-order Trotter, synthetic "
+                                   "right-canonical chi=64 start states" % n_traj,
+                       "precision": "mixed: complex64 tensors and Jacobi rotations; float64 "
+                                    "singular values, norms, Lambda, jump rates",
+                       "l2": "inputs larger than L2 (17 GB of site tensors), no flush",
+                       "parallelism": "trajectories sharded over %d GPU(s)" % world},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "trajectory_steps_per_s": world * n_traj * args.steps / (total_ms / 1e3),
+            "roofline": {"bound": "alu", "kernel": "bond_update_kernel<float>",
+                         "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "peak_source": "FP32 FMA lanes: 148 SM x 128 x 2 flop x sm_max_mhz "
+                                        "(%s clock)" % src,
+                         "mean_layer_ms": mean_layer_s * 1e3,
+                         "flops_per_layer": flops_per_layer},
+            "jacobi_sweeps_mean": sweeps_mean,
+            "fp64_path": fp64,
+            "speedup_vs_fp64": (value / world / fp64["updates_per_s"]) if fp64 else None,
+            "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -82,7 +82,7 @@ typedef struct {
   uint64_t seed;             /* Philox4x32-10 key                                  */
   int64_t traj_offset;       /* global id of trajectory 0 (Philox counter word 0)  */
   double jacobi_tol;         /* rotate a row pair while |x.y^+| > tol |x| |y|;     */
-                             /* 0 = default 4 eps sqrt(n) of the working precision */
+                             /* 0 = default eps sqrt(n) of the working precision   */
 } lt_config;
 
 /* Create a context: validate cfg, allocate the ensemble on the current device
@@ -162,6 +162,18 @@ lt_status lt_load(lt_ctx ctx, const char* path);
  * (index s, the last bin collects s >= 63) since the context was created or
  * the histogram was last cleared; clear != 0 resets it after reading. */
 lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear);
+
+/* Work counters of the two-site update since creation or the last clear:
+ * out[0] two-site updates executed (all), out[1] Jacobi rotations applied,
+ * out[2] Jacobi row-pair inner products, out[3] algorithmic real floating-point
+ * operations of the updates in Trotter layers, out[4] the same for the
+ * identity-gate updates that restore the canonical form after jumps,
+ * out[5] two-site updates executed in Trotter layers.  The operation count of
+ * one update with theta of m x n, middle dimension chi_M, k kept values and s
+ * sweeps is 8 m n (chi_M + 4) + 4 m n (s + 1) + 8 n P + 24 n Rot + 8 m k n,
+ * P = s m (m - 1) / 2 inner products and Rot applied rotations.  clear != 0
+ * resets the counters after reading.  out: [6] or NULL. */
+lt_status lt_get_counters(lt_ctx ctx, uint64_t* out, int32_t clear);
 
 /* Number of kernels this context has launched so far. */
 int64_t lt_launch_count(lt_ctx ctx);

@@ -149,7 +149,7 @@ template <typename T> lt_status dalloc(lt_ctx_s* c, T** p, size_t n) {
 void free_all(lt_ctx_s* c) {
   void* ptrs[] = {c->B, c->lam, c->dims, c->trunc, c->evolve, c->channel, c->replay,
                   c->active_list, c->jumped_list, c->counts, c->density, c->rates, c->gam,
-                  c->err_dev, c->sweep_hist, c->gates, c->bond_scratch, c->env_scratch,
+                  c->err_dev, c->sweep_hist, c->counters, c->gates, c->bond_scratch, c->env_scratch,
                   c->corr, c->red};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -188,6 +188,17 @@ lt_status lt_get_sweep_histogram(lt_ctx c, int32_t* hist, int32_t clear) {
   if (st != LT_OK) return st;
   if (hist) LT_CK(cudaMemcpyAsync(hist, c->sweep_hist, 64 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (clear) LT_CK(cudaMemsetAsync(c->sweep_hist, 0, 64 * sizeof(int), c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
+  return LT_OK;
+}
+
+lt_status lt_get_counters(lt_ctx c, uint64_t* out, int32_t clear) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (out)
+    LT_CK(cudaMemcpyAsync(out, c->counters, LT_NCOUNTERS * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, c->stream));
+  if (clear) LT_CK(cudaMemsetAsync(c->counters, 0, LT_NCOUNTERS * sizeof(unsigned long long), c->stream));
   LT_CK(cudaStreamSynchronize(c->stream));
   return LT_OK;
 }
@@ -285,6 +296,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (st == LT_OK) st = dalloc(c, &c->gam, 3 * (size_t)L);
   if (st == LT_OK) st = dalloc(c, &c->err_dev, 1);
   if (st == LT_OK) st = dalloc(c, &c->sweep_hist, 64);
+  if (st == LT_OK) st = dalloc(c, &c->counters, LT_NCOUNTERS);
   if (st == LT_OK) st = dalloc(c, &c->gates, 8 * nb * 16);
   if (st == LT_OK) st = dalloc(c, &c->red, 2 * (size_t)L * L + 2 * (size_t)L);
   if (st == LT_OK && !c->bond_use_smem)
@@ -306,6 +318,8 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->lam, 0, nt * nb * c->chi * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sweep_hist, 0, 64 * sizeof(int), c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(c->counters, 0, LT_NCOUNTERS * sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = launch_init_state(c, occ_dev);
     if (e == cudaSuccess) e = launch_compact(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -12,6 +12,7 @@
 #define LT_MAX_CHI 64
 #define LT_MAX_DIM (2 * LT_MAX_CHI)  // largest theta side, d * chi_max
 #define LT_BLOCK 256
+#define LT_NCOUNTERS 6
 
 // device error bits (ctx->err_dev)
 #define LT_EBIT_THETA_ZERO 1   // a theta matrix vanished
@@ -115,6 +116,7 @@ template <typename R> struct BondArgs {
   int max_sweeps;
   double tol;            // Jacobi threshold, 0 = 4 eps sqrt(n)
   int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
+  unsigned long long* counters;  // see lt_get_counters
 };
 
 struct EnvArgs {
@@ -172,6 +174,7 @@ struct lt_ctx_s {
   double* gam;      // [3][L]
   int* err_dev;
   int* sweep_hist;  // [64]
+  unsigned long long* counters;  // [LT_NCOUNTERS]
 
   // gate cache: up to 8 distinct tau values
   std::vector<double> gate_taus;

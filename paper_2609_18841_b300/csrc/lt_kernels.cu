@@ -91,7 +91,7 @@ __device__ __forceinline__ void rr_pair(int round, int i, int m, int& p, int& q)
 // sigma_r v_r^+ for the right singular vectors v_r of the input.  Returns sweeps.
 template <typename R>
 __device__ int jacobi_rows(typename CT<R>::T* X, int ld, int m, int n, R* nrm, int* flag,
-                           int max_sweeps, double tol_override) {
+                           int* nrot, int max_sweeps, double tol_override) {
   typedef typename CT<R>::T Tc;
   int gs = 1;
   while (gs * 4 < n && gs < 32) gs <<= 1;
@@ -99,7 +99,7 @@ __device__ int jacobi_rows(typename CT<R>::T* X, int ld, int m, int n, R* nrm, i
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int npairs = m / 2;
   const int iters = (npairs + ng - 1) / ng;
-  const R tol = tol_override > 0.0 ? (R)tol_override : (R)4 * Eps<R>::v * sqrt((R)n);
+  const R tol = tol_override > 0.0 ? (R)tol_override : Eps<R>::v * sqrt((R)n);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     __syncthreads();
@@ -155,6 +155,7 @@ __device__ int jacobi_rows(typename CT<R>::T* X, int ld, int m, int n, R* nrm, i
               nrm[p] = alpha - t * ga;
               nrm[q] = beta + t * ga;
               *flag = 1;
+              atomicAdd(nrot, 1);
             }
           }
         }
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
   __shared__ int s_perm[LT_MAX_DIM];
   __shared__ Tc s_gate[16];
   __shared__ double s_lamL[LT_MAX_CHI];
-  __shared__ int s_flag, s_k;
+  __shared__ int s_flag, s_k, s_nrot;
   __shared__ double s_norm, s_wdisc;
 
   Tc* X = a.use_smem ? reinterpret_cast<Tc*>(smem_raw) : a.scratch + (long long)blockIdx.x * a.scratch_stride;
@@ -209,9 +210,10 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
     }
     for (int i = tid; i < chiL; i += blockDim.x)
       s_lamL[i] = b == 0 ? 1.0 : a.lam[((long long)traj * (L - 1) + b - 1) * chi + i];
+    if (tid == 0) s_nrot = 0;
     __syncthreads();
     form_theta<R>(X, ld, Bl, Br, chiL, chiM, chiR, s_gate, s_lamL, true);
-    const int sweeps = jacobi_rows<R>(X, ld, m, n, s_nrm, &s_flag, a.max_sweeps, a.tol);
+    const int sweeps = jacobi_rows<R>(X, ld, m, n, s_nrm, &s_flag, &s_nrot, a.max_sweeps, a.tol);
     // singular values squared, accumulated in double
     {
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -255,6 +257,19 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
       s_norm = kept > 0.0 ? sqrt(kept) : 1.0;
       s_wdisc = total > 0.0 ? (total - kept) / total : 0.0;
       if (a.sweep_hist) atomicAdd(a.sweep_hist + (sweeps < 63 ? sweeps : 63), 1);
+      if (a.counters) {
+        // algorithmic real flops: theta (once) + Jacobi (row norms, one complex
+        // dot per pair per sweep, 24n per applied rotation, final norms) + split
+        const double dm_ = m, dn_ = n;
+        const double pairs = 0.5 * dm_ * (dm_ - 1.0) * sweeps;
+        const double fl = 8.0 * dm_ * dn_ * (chiM + 4) + 4.0 * dm_ * dn_ * (sweeps + 1) +
+                          8.0 * dn_ * pairs + 24.0 * dn_ * s_nrot + 8.0 * dm_ * k * dn_;
+        atomicAdd(a.counters + 0, 1ull);
+        atomicAdd(a.counters + 1, (unsigned long long)s_nrot);
+        atomicAdd(a.counters + 2, (unsigned long long)pairs);
+        atomicAdd(a.counters + (a.gates ? 3 : 4), (unsigned long long)fl);
+        if (a.gates) atomicAdd(a.counters + 5, 1ull);
+      }
       if (sweeps > a.max_sweeps) atomicOr(a.err, LT_EBIT_NOCONV);
     }
     __syncthreads();
@@ -717,6 +732,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.max_sweeps = c->max_sweeps;
   a.tol = c->jacobi_tol;
   a.sweep_hist = c->sweep_hist;
+  a.counters = c->counters;
   bond_update_kernel<R><<<c->bond_grid, LT_BLOCK, c->bond_use_smem ? c->bond_smem : 0, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
