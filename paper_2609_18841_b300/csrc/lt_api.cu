@@ -112,7 +112,8 @@ lt_status gate_ptr(lt_ctx_s* c, double tau, const double2** out) {
   build_gates(c, tau, h);
   const size_t i = c->gate_taus.size();
   double2* dst = c->gates + i * (size_t)(c->L - 1) * 16;
-  LT_CK(cudaMemcpy(dst, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  LT_CK(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
   c->gate_taus.push_back(tau);
   *out = dst;
   return LT_OK;
@@ -128,7 +129,7 @@ lt_status check_device_error(lt_ctx_s* c) {
   if (err & LT_EBIT_BADARG) {
     c->last_error = "replayed channel out of range";
     int zero = 0;
-    LT_CK(cudaMemcpy(c->err_dev, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    LT_CK(cudaMemcpyAsync(c->err_dev, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     return LT_ERR_ARG;
   }
   return LT_OK;
@@ -312,8 +313,8 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
       g[L + i] = c->gg[i];
       g[2 * L + i] = c->gd[i];
     }
-    e = cudaMemcpy(c->gam, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(occ_dev, c->occ.data(), L, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(c->gam, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(occ_dev, c->occ.data(), L, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->B, 0, nt * L * c->slot * c->celt, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->lam, 0, nt * nb * c->chi * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
@@ -362,8 +363,12 @@ lt_status lt_apply_jumps(lt_ctx c, int64_t step, const int32_t* replay, int32_t*
   lt_status st = guard(c);
   if (st != LT_OK) return st;
   if (step < 0) return LT_ERR_ARG;
-  if (replay)
-    LT_CK(cudaMemcpyAsync(c->replay, replay, sizeof(int) * c->n_traj, cudaMemcpyHostToDevice, c->stream));
+  if (replay) {
+    // stage through pageable host memory: the caller's array is consumed before return
+    c->replay_host.assign(replay, replay + c->n_traj);
+    LT_CK(cudaMemcpyAsync(c->replay, c->replay_host.data(), sizeof(int) * c->n_traj,
+                          cudaMemcpyHostToDevice, c->stream));
+  }
   LT_CK(launch_env(c, 1, step, replay ? c->replay : nullptr));
   LT_CK(launch_compact(c));
   LT_CK(launch_jump_apply(c));
@@ -483,10 +488,9 @@ lt_status lt_set_state(lt_ctx c, int32_t traj0, int32_t n, const int32_t* dims, 
   for (size_t i = 0; i < (size_t)n * nb; ++i)
     if (dims[i] < 1 || dims[i] > c->chi) return LT_ERR_ARG;
   LT_CK(cudaStreamSynchronize(c->stream));
-  LT_CK(cudaMemcpy(c->dims + (size_t)traj0 * nb, dims, sizeof(int) * n * nb, cudaMemcpyHostToDevice));
-  LT_CK(cudaMemcpy(c->lam + (size_t)traj0 * nb * c->chi, lam, sizeof(double) * n * nb * c->chi,
-                   cudaMemcpyHostToDevice));
-  LT_CK(cudaMemset(c->trunc + (size_t)traj0 * nb, 0, sizeof(double) * n * nb));
+  LT_CK(cudaMemcpyAsync(c->dims + (size_t)traj0 * nb, dims, sizeof(int) * n * nb, cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaMemcpyAsync(c->lam + (size_t)traj0 * nb * c->chi, lam, sizeof(double) * n * nb * c->chi, cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaMemsetAsync(c->trunc + (size_t)traj0 * nb, 0, sizeof(double) * n * nb, c->stream));
   const long long per_traj = (long long)c->L * c->slot;
   const int chunk = 8;
   double* stage = nullptr;
@@ -494,8 +498,7 @@ lt_status lt_set_state(lt_ctx c, int32_t traj0, int32_t n, const int32_t* dims, 
   if (st != LT_OK) return st;
   for (int t = 0; t < n && st == LT_OK; t += chunk) {
     const int m = n - t < chunk ? n - t : chunk;
-    cudaError_t e = cudaMemcpy(stage, B + 2 * (size_t)per_traj * t, sizeof(double) * 2 * per_traj * m,
-                               cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(stage, B + 2 * (size_t)per_traj * t, sizeof(double) * 2 * per_traj * m, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_convert_in(c, stage, per_traj * m, per_traj * (traj0 + t));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_set_state", cudaGetErrorString(e));
@@ -510,10 +513,10 @@ lt_status lt_get_state(lt_ctx c, int32_t traj0, int32_t n, int32_t* dims, double
   if (traj0 < 0 || n < 0 || traj0 + (long long)n > c->n_traj) return LT_ERR_ARG;
   const size_t nb = c->L - 1;
   LT_CK(cudaStreamSynchronize(c->stream));
-  if (dims) LT_CK(cudaMemcpy(dims, c->dims + (size_t)traj0 * nb, sizeof(int) * n * nb, cudaMemcpyDeviceToHost));
+  if (dims) LT_CK(cudaMemcpyAsync(dims, c->dims + (size_t)traj0 * nb, sizeof(int) * n * nb, cudaMemcpyDeviceToHost, c->stream));
   if (lam)
-    LT_CK(cudaMemcpy(lam, c->lam + (size_t)traj0 * nb * c->chi, sizeof(double) * n * nb * c->chi,
-                     cudaMemcpyDeviceToHost));
+    LT_CK(cudaMemcpyAsync(lam, c->lam + (size_t)traj0 * nb * c->chi, sizeof(double) * n * nb * c->chi, cudaMemcpyDeviceToHost, c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
   if (!B) return LT_OK;
   const long long per_traj = (long long)c->L * c->slot;
   const int chunk = 8;
@@ -525,8 +528,7 @@ lt_status lt_get_state(lt_ctx c, int32_t traj0, int32_t n, int32_t* dims, double
     cudaError_t e = launch_convert_out(c, stage, per_traj * m, per_traj * (traj0 + t));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpy(B + 2 * (size_t)per_traj * t, stage, sizeof(double) * 2 * per_traj * m,
-                     cudaMemcpyDeviceToHost);
+      e = cudaMemcpyAsync(B + 2 * (size_t)per_traj * t, stage, sizeof(double) * 2 * per_traj * m, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_get_state", cudaGetErrorString(e));
   }
   cudaFree(stage);
@@ -544,10 +546,11 @@ lt_status lt_save(lt_ctx c, const char* path) {
   std::vector<double> lam(nt * nb * c->chi), tr(nt * nb);
   std::vector<char> B(nt * c->L * c->slot * c->celt);
   LT_CK(cudaStreamSynchronize(c->stream));
-  LT_CK(cudaMemcpy(dims.data(), c->dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  LT_CK(cudaMemcpy(lam.data(), c->lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  LT_CK(cudaMemcpy(tr.data(), c->trunc, tr.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  LT_CK(cudaMemcpy(B.data(), c->B, B.size(), cudaMemcpyDeviceToHost));
+  LT_CK(cudaMemcpyAsync(dims.data(), c->dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LT_CK(cudaMemcpyAsync(lam.data(), c->lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LT_CK(cudaMemcpyAsync(tr.data(), c->trunc, tr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LT_CK(cudaMemcpyAsync(B.data(), c->B, B.size(), cudaMemcpyDeviceToHost, c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(c, LT_ERR_ARG, "lt_save", "cannot open file");
   const char magic[8] = {'L', 'T', 'C', 'K', 'P', 'T', '0', '1'};
@@ -588,10 +591,11 @@ lt_status lt_load(lt_ctx c, const char* path) {
   for (int d : dims)
     if (d < 1 || d > c->chi) return fail(c, LT_ERR_ARG, "lt_load", "bond dimension out of range");
   LT_CK(cudaStreamSynchronize(c->stream));
-  LT_CK(cudaMemcpy(c->dims, dims.data(), dims.size() * sizeof(int), cudaMemcpyHostToDevice));
-  LT_CK(cudaMemcpy(c->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
-  LT_CK(cudaMemcpy(c->trunc, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice));
-  LT_CK(cudaMemcpy(c->B, B.data(), B.size(), cudaMemcpyHostToDevice));
+  LT_CK(cudaMemcpyAsync(c->dims, dims.data(), dims.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaMemcpyAsync(c->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaMemcpyAsync(c->trunc, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaMemcpyAsync(c->B, B.data(), B.size(), cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaStreamSynchronize(c->stream));
   c->step_counter = stepc;
   return LT_OK;
 }

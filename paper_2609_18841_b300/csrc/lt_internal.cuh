@@ -151,6 +151,7 @@ struct lt_ctx_s {
   long long traj_offset;
   std::vector<double> gl, gg, gd;
   std::vector<uint8_t> occ;
+  std::vector<int> replay_host;
   int init;
 
   cudaStream_t stream;
