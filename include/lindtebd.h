@@ -175,6 +175,40 @@ lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear)
  * resets the counters after reading.  out: [6] or NULL. */
 lt_status lt_get_counters(lt_ctx ctx, uint64_t* out, int32_t clear);
 
+/* Allocation-free variant of the per-trajectory density measurement, for
+ * callers that cannot call cudaMalloc: processes whose device memory is owned
+ * by another allocator (a framework's caching allocator, or a serving runtime
+ * that reserves the GPU's memory up front), where an extra cudaMalloc either
+ * fails or takes memory the owner has promised elsewhere, and callers that
+ * cannot accept the device-wide synchronisation cudaMalloc/cudaFree may cause.
+ * The paper has no counterpart; it is an interface convenience.
+ *
+ * Computes <n_i> = <psi|n_i|psi>/<psi|psi> (the densities lt_measure_density
+ * returns per trajectory) for an MPS ensemble the caller holds on the current
+ * device, in the library's layout: B [n_traj][L][2 chi_max^2] complex
+ * (float2 for LT_MIXED, double2 for LT_FP64, site i holding B_i[a][s][c]
+ * row-major over its actual shape), dims [n_traj][L-1] int32 with
+ * 1 <= dims <= chi_max, density [n_traj][L] double (written).  All three are
+ * DEVICE pointers owned by the caller.  Work is queued on `stream` (a
+ * cudaStream_t, NULL = the legacy default stream); the call does not
+ * synchronise it and calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ * Scratch: a 32 MiB array in the library's static device memory, present on
+ * every GPU that loads the library until the process exits.  One trajectory
+ * needs (L + 8) * chi_max^2 complex elements of it, so the call returns
+ * LT_ERR_ARG when (L + 8) chi_max^2 * 8 bytes (LT_MIXED) or * 16 bytes (LT_FP64)
+ * exceeds 32 MiB (e.g. LT_FP64 with L > 504 at chi_max = 64), and LT_ERR_ARG for
+ * any other invalid size or NULL pointer.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  Every call shares the one
+ * array and the kernel writes each scratch element before reading it, so
+ * nothing needs clearing between calls; calls that overlap on the GPU (on
+ * different streams, or from several threads) race on it and must be
+ * serialised by the caller. */
+lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, int32_t chi_max,
+                                     int32_t n_traj, const void* B, const int32_t* dims,
+                                     double* density, void* stream);
+
 /* Number of kernels this context has launched so far. */
 int64_t lt_launch_count(lt_ctx ctx);
 

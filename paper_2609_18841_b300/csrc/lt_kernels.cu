@@ -13,6 +13,8 @@
 //  corr_kernel         C_ij = <c_i^+ c_j> by transfer matrices.
 #include <cfloat>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 
 #include "lt_internal.cuh"
 
@@ -380,8 +382,9 @@ __device__ double right_envs(const typename CT<R>::T* B, const int* dm, int L, i
   return (double)Rl[0].x;
 }
 
-// env_kernel: per trajectory, exact <n_k> for every site, rates and decision.
-template <typename R>
+// env_kernel: per trajectory, exact <n_k> for every site, rates and decision
+// (kRates = false: densities only).
+template <typename R, bool kRates = true>
 __global__ void __launch_bounds__(LT_BLOCK) env_kernel(EnvArgs a) {
   typedef typename CT<R>::T Tc;
   __shared__ double red[32];
@@ -414,17 +417,19 @@ __global__ void __launch_bounds__(LT_BLOCK) env_kernel(EnvArgs a) {
       if (threadIdx.x == 0) {
         const double nk = d.x / nrm2;
         a.density[(long long)traj * L + k] = nk;
-        double* rt = a.rates + (long long)traj * 3 * L + 3 * k;
-        rt[0] = a.gl[k] * nk;
-        rt[1] = a.gg[k] * (1.0 - nk);
-        rt[2] = a.gd[k] * nk;
+        if (kRates) {
+          double* rt = a.rates + (long long)traj * 3 * L + 3 * k;
+          rt[0] = a.gl[k] * nk;
+          rt[1] = a.gg[k] * (1.0 - nk);
+          rt[2] = a.gd[k] * nk;
+        }
       }
       __syncthreads();
       Tc* tmp = Le;
       Le = Ln;
       Ln = tmp;
     }
-    if (a.decide && threadIdx.x == 0) {
+    if (kRates && a.decide && threadIdx.x == 0) {
       const double* rt = a.rates + (long long)traj * 3 * L;
       int ch = -1;
       const int rep = a.replay ? a.replay[traj] : -2;
@@ -889,4 +894,65 @@ cudaError_t configure_bond(lt_ctx_s* c) {
   c->bond_grid = occ * c->num_sms;
   c->bond_scratch_stride = c->bond_use_smem ? 0 : (long long)(need / c->celt);
   return cudaSuccess;
+}
+
+// ---- allocation-free density entry point -------------------------------------------------
+// Scratch of lt_measure_density_noalloc: a file-scope device array, so that the
+// call itself allocates nothing.  Every GPU that loads the library holds it until
+// the process exits.
+#define LT_NOALLOC_SCRATCH_BYTES (32ull << 20)
+#define LT_NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) unsigned char lt_noalloc_scratch[LT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[LT_NOALLOC_MAX_DEVICES];
+}  // namespace
+
+extern "C" lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, int32_t chi_max,
+                                                int32_t n_traj, const void* B,
+                                                const int32_t* dims, double* density,
+                                                void* stream) {
+  if (L < 2 || L > 1024 || chi_max < 1 || chi_max > LT_MAX_CHI || n_traj < 1 ||
+      (precision != LT_FP64 && precision != LT_MIXED) || !B || !dims || !density)
+    return LT_ERR_ARG;
+  const size_t celt = precision == LT_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t stride = env_scratch_elems(L, chi_max);
+  const size_t per_cta = stride * celt;
+  if (per_cta > LT_NOALLOC_SCRATCH_BYTES) return LT_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LT_ERR_CUDA;
+  if (dev < 0 || dev >= LT_NOALLOC_MAX_DEVICES) return LT_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  {
+    // once per device, with that device current: the host-side name of the
+    // array is only a stand-in, the kernel needs its device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, lt_noalloc_scratch) != cudaSuccess || !p) return LT_ERR_CUDA;
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LT_ERR_CUDA;
+  long long grid = (long long)(LT_NOALLOC_SCRATCH_BYTES / per_cta);
+  if (grid > 2LL * sms) grid = 2LL * sms;
+  if (grid > n_traj) grid = n_traj;
+  EnvArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.B = const_cast<void*>(B);
+  a.dims = dims;
+  a.L = L;
+  a.chi = chi_max;
+  a.slot = 2 * chi_max * chi_max;
+  a.n_traj = n_traj;
+  a.scratch = scratch;
+  a.scratch_stride = (long long)stride;
+  a.density = density;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == LT_MIXED) env_kernel<float, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
+  else env_kernel<double, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? LT_OK : LT_ERR_CUDA;
 }

@@ -38,7 +38,7 @@ class lt_config(ctypes.Structure):
 
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
            "lt_step", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
-           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_launch_count", "lt_stream", "lt_get_step",
+           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
            "lt_status_str", "lt_last_error"]
 
 
@@ -63,6 +63,7 @@ def load_library(path=LIB_PATH):
         "lt_load": ([P, ctypes.c_char_p], I32),
         "lt_get_sweep_histogram": ([P, P, I32], I32),
         "lt_get_counters": ([P, P, I32], I32),
+        "lt_measure_density_noalloc": ([I32, I32, I32, I32, P, P, P, P], I32),
         "lt_launch_count": ([P], I64),
         "lt_stream": ([P], P),
         "lt_get_step": ([P], I64),
@@ -214,6 +215,13 @@ def lt_get_counters(ctx, clear=False):
     c = np.zeros(6, np.uint64)
     _check(_lib.lt_get_counters(ctx, _ptr(c), int(clear)), "lt_get_counters", ctx)
     return dict(zip(COUNTER_NAMES, (int(x) for x in c)))
+
+
+def lt_measure_density_noalloc(precision, L, chi_max, n_traj, B_ptr, dims_ptr, density_ptr,
+                               stream=None):
+    """Device pointers in, densities written to density_ptr; returns the status."""
+    return int(_lib.lt_measure_density_noalloc(precision, L, chi_max, n_traj, B_ptr, dims_ptr,
+                                               density_ptr, stream))
 
 
 def lt_launch_count(ctx):
