@@ -9,6 +9,7 @@
 #include "lt_internal.cuh"
 
 cudaError_t configure_bond(lt_ctx_s* c);
+int env_grid(lt_ctx_s* c);
 
 namespace {
 
@@ -280,7 +281,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   const size_t nt = c->n_traj, nb = L - 1;
   e = configure_bond(c);
   if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "configure_bond", cudaGetErrorString(e));
-  c->env_grid = 2 * c->num_sms < c->n_traj ? 2 * c->num_sms : c->n_traj;
+  c->env_grid = env_grid(c);
   c->env_scratch_stride = (long long)env_scratch_elems(L, c->chi);
   if (st == LT_OK) st = dalloc(c, (char**)&c->B, nt * L * c->slot * c->celt);
   if (st == LT_OK) st = dalloc(c, &c->lam, nt * nb * c->chi);

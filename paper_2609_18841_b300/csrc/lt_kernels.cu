@@ -39,39 +39,105 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
   return s;
 }
 
+// ---- packed pairs of reals ----------------------------------------------------------------
+// Two adjacent elements of one plane (real or imaginary parts) as a float2 go
+// through Blackwell's packed single-precision FMA (IEEE round-to-nearest per
+// lane); double2 falls back to two scalar FMAs.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+template <typename V, typename R> __device__ __forceinline__ V splat(R v) {
+  V r;
+  r.x = v;
+  r.y = v;
+  return r;
+}
+
 // ---- theta formation (Eq. Theta) -----------------------------------------------------
-// X[(a,s'),(t',c)] = w_a sum_{s,t} G[s't',st] sum_mu Bl[a,s,mu] Br[mu,t,c]
+// theta[(a,s'),(t',c)] = w_a sum_{s,t} G[s't',st] sum_mu Bl[a,s,mu] Br[mu,t,c], written
+// planar (real parts in Xr, imaginary parts in Xi, row stride ldp).  Br is first
+// staged in shared memory (Bs_in, chiM x 2chiR) when a staging area is given;
+// each thread computes two values of a for one column c, so consecutive lanes
+// read consecutive Bs words and share the broadcast Bl reads.  Columns n..npad-1
+// are set to zero (the Jacobi sweeps run over npad columns without tests), and
+// so are the padding rows 2 chiL .. mp-1.
 template <typename R>
-__device__ void form_theta(typename CT<R>::T* X, int ldx, const typename CT<R>::T* Bl,
-                           const typename CT<R>::T* Br, int chiL, int chiM, int chiR,
-                           const typename CT<R>::T* G, const double* lamL, bool weighted) {
+__device__ void form_theta(R* Xr, R* Xi, int ldp, int npad, int mp, const typename CT<R>::T* Bl,
+                           const typename CT<R>::T* Br, const typename CT<R>::T* Bs_in, int chiL,
+                           int chiM, int chiR, const typename CT<R>::T* G, const double* lamL,
+                           bool weighted) {
   typedef typename CT<R>::T Tc;
   const int n2 = 2 * chiR;
-  for (int idx = threadIdx.x; idx < chiL * chiR; idx += blockDim.x) {
-    const int a = idx / chiR, c = idx - a * chiR;
-    Tc p00 = czero<Tc>(), p01 = czero<Tc>(), p10 = czero<Tc>(), p11 = czero<Tc>();
-    const Tc* l0 = Bl + (2 * a) * chiM;
-    const Tc* l1 = l0 + chiM;
-    for (int mu = 0; mu < chiM; ++mu) {
-      const Tc x0 = l0[mu], x1 = l1[mu];
-      const Tc y0 = Br[mu * n2 + c], y1 = Br[mu * n2 + chiR + c];
-      cfma(p00, x0, y0);
-      cfma(p01, x0, y1);
-      cfma(p10, x1, y0);
-      cfma(p11, x1, y1);
+  if (npad > n2) {
+    const int w = npad - n2;
+    for (int i = threadIdx.x; i < 2 * chiL * w; i += blockDim.x) {
+      const int r = i / w, c = n2 + (i - r * w);
+      Xr[r * ldp + c] = (R)0;
+      Xi[r * ldp + c] = (R)0;
     }
-    const R w = weighted ? (R)lamL[a] : (R)1;
+  }
+  for (int i = threadIdx.x; i < (mp - 2 * chiL) * npad; i += blockDim.x) {
+    const int r = 2 * chiL + i / npad, c = i - (i / npad) * npad;
+    Xr[r * ldp + c] = (R)0;
+    Xi[r * ldp + c] = (R)0;
+  }
+  const Tc* Bs = Bs_in;
+  if (Bs_in) {
+    Tc* st = const_cast<Tc*>(Bs_in);
+    for (int i = threadIdx.x; i < chiM * n2; i += blockDim.x) st[i] = Br[i];
+    __syncthreads();
+  } else {
+    Bs = Br;  // no room to stage: read B_{b+1} through L1
+  }
+  const int ahalf = (chiL + 1) >> 1;
+  for (int idx = threadIdx.x; idx < ahalf * chiR; idx += blockDim.x) {
+    const int a0 = idx / chiR, c = idx - a0 * chiR;
+    const int a1 = a0 + ahalf;
+    const bool two = a1 < chiL;
+    Tc p[2][4];
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
+    for (int u = 0; u < 2; ++u)
 #pragma unroll
-      for (int tp = 0; tp < 2; ++tp) {
-        const Tc* g = G + (sp * 2 + tp) * 4;
-        Tc v = czero<Tc>();
-        cfma(v, g[0], p00);
-        cfma(v, g[1], p01);
-        cfma(v, g[2], p10);
-        cfma(v, g[3], p11);
-        X[(2 * a + sp) * ldx + tp * chiR + c] = cscale(v, w);
+      for (int v = 0; v < 4; ++v) p[u][v] = czero<Tc>();
+    const Tc* l00 = Bl + (2 * a0) * chiM;
+    const Tc* l10 = Bl + (2 * (two ? a1 : a0)) * chiM;
+    for (int mu = 0; mu < chiM; ++mu) {
+      const Tc y0 = Bs[mu * n2 + c], y1 = Bs[mu * n2 + chiR + c];
+      const Tc x0 = l00[mu], x1 = l00[chiM + mu];
+      const Tc z0 = l10[mu], z1 = l10[chiM + mu];
+      cfma(p[0][0], x0, y0);
+      cfma(p[0][1], x0, y1);
+      cfma(p[0][2], x1, y0);
+      cfma(p[0][3], x1, y1);
+      cfma(p[1][0], z0, y0);
+      cfma(p[1][1], z0, y1);
+      cfma(p[1][2], z1, y0);
+      cfma(p[1][3], z1, y1);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      const int a = u ? a1 : a0;
+      const R w = weighted ? (R)lamL[a] : (R)1;
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+        for (int tp = 0; tp < 2; ++tp) {
+          const Tc* g = G + (sp * 2 + tp) * 4;
+          Tc v = czero<Tc>();
+          cfma(v, g[0], p[u][0]);
+          cfma(v, g[1], p[u][1]);
+          cfma(v, g[2], p[u][2]);
+          cfma(v, g[3], p[u][3]);
+          const int o = (2 * a + sp) * ldp + tp * chiR + c;
+          Xr[o] = v.x * w;
+          Xi[o] = v.y * w;
+        }
       }
     }
   }
@@ -88,92 +154,358 @@ __device__ __forceinline__ void rr_pair(int round, int i, int m, int& p, int& q)
   }
 }
 
-// One-sided Jacobi on the m rows of X (length n): unitary 2x2 rotations of row
-// pairs until every pair is orthogonal to tol * |x| |y|.  Afterwards row r holds
-// sigma_r v_r^+ for the right singular vectors v_r of the input.  Returns sweeps.
+// One-sided Jacobi on the m rows of the planar matrix (Xr, Xi), length n:
+// unitary 2x2 rotations of row pairs until every pair is orthogonal to
+// tol * |x| |y|.  Afterwards row r holds sigma_r v_r^+ for the right singular
+// vectors v_r of the input.  Returns the number of sweeps.
+//
+// A pair is handled by gs lanes; each lane holds EPP element pairs of both
+// rows (real and imaginary planes) in registers, so every element is loaded
+// once and, when the pair rotates, stored once.  Packed FMAs work on two
+// elements at a time: the inner product is 2 and the rotation 6 instructions
+// per element.  All m/2 pairs of a round run at once when the block has enough
+// groups; with 8-lane groups the two groups of a half-warp take rows 8 apart,
+// which with the row stride n + 2 puts their windows in disjoint banks.
+// 1/sqrt(x): single precision refines the hardware estimate y by the residual
+// form y + y (1 - x y^2) / 2 (within about one ulp, so the rotations stay
+// unitary to working precision); double precision divides.
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  const float y = rsqrtf(x);
+  const float r = fmaf(-x * y, y, 1.0f);
+  return fmaf(0.5f * y, r, y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) { return 1.0 / sqrt(x); }
+
+// Parameters of the 2x2 unitary that orthogonalises rows x, y with squared
+// norms alpha, beta and inner product g = x . y^+ (gx + i gy):
+//   zeta = (beta - alpha) / (2|g|),  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+//   c = 1/sqrt(1 + t^2),  s e^{i phi} = c t g/|g|;
+// the squared norms become alpha - t|g| and beta + t|g|.  Returns false when the
+// pair is already orthogonal to tol |x| |y| (or a row vanishes).  One division;
+// the reciprocal square roots are refined to about one ulp.
 template <typename R>
-__device__ int jacobi_rows(typename CT<R>::T* X, int ld, int m, int n, R* nrm, int* flag,
-                           int* nrot, int max_sweeps, double tol_override) {
-  typedef typename CT<R>::T Tc;
+__device__ __forceinline__ bool rot_params(R gx, R gy, R alpha, R beta, R tol, R& cs, R& sex,
+                                           R& sey, R& tga) {
+  const R g2 = gx * gx + gy * gy;
+  if (!(alpha > (R)0 && beta > (R)0 && g2 > tol * tol * alpha * beta)) return false;
+  const R inv = rsqrt_nr(g2);
+  const R zeta = (beta - alpha) * (R)0.5 * inv;
+  const R az = fabs(zeta);
+  const R root = az < (R)1e18 ? sqrt(fma(zeta, zeta, (R)1)) : az;
+  const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (az + root);
+  cs = rsqrt_nr(fma(t, t, (R)1));
+  const R sn = cs * t;
+  sex = sn * gx * inv;
+  sey = sn * gy * inv;
+  tga = t * (g2 * inv);
+  return true;
+}
+
+template <typename R, int EPP>
+__device__ __forceinline__ int jacobi_span(int n) {
   int gs = 1;
-  while (gs * 4 < n && gs < 32) gs <<= 1;
+  while (gs * 2 * EPP < n && gs < 32) gs <<= 1;
+  return gs;
+}
+
+template <typename R, int EPP>
+__device__ int jacobi_rows(R* Xr, R* Xi, int ldp, int m, int n, R* nrm, int* nrot, int max_sweeps,
+                           double tol_override) {
+  typedef typename CT<R>::T V;  // a pair of reals of one plane
+  const int gs = jacobi_span<R, EPP>(n);
   const int ng = blockDim.x / gs, gid = threadIdx.x / gs, gl = threadIdx.x - gid * gs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int npairs = m / 2;
   const int iters = (npairs + ng - 1) / ng;
+  const bool remap = gs == 8 && ng == 64 && npairs == 64;
   const R tol = tol_override > 0.0 ? (R)tol_override : Eps<R>::v * sqrt((R)n);
+  // partner rows of this group's pair in round 0; when every pair of a round
+  // has its own group they advance by one (mod m-1) per round
+  const int pi0 = remap ? (((gid >> 4) << 4) | ((gid & 1) << 3) | ((gid >> 1) & 7)) : gid;
+  int p0 = 0, q0 = 0;
+  if (gid < npairs) rr_pair(0, pi0, m, p0, q0);
+  int my_rot = 0;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     __syncthreads();
-    if (threadIdx.x == 0) *flag = 0;
     for (int r = warp; r < m; r += nw) {
       R acc = 0;
       for (int c = lane; c < n; c += 32) {
-        const Tc v = X[r * ld + c];
-        acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+        const R u = Xr[r * ldp + c], v = Xi[r * ldp + c];
+        acc = fma(u, u, fma(v, v, acc));
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
       if (lane == 0) nrm[r] = acc;
     }
     __syncthreads();
+    int any = 0;
+    int pr = p0, qr = q0;
     for (int round = 0; round < m - 1; ++round) {
       for (int it = 0; it < iters; ++it) {
-        const int pi = it * ng + gid;
-        const bool valid = pi < npairs;
-        int p = 0, q = 0;
-        if (valid) rr_pair(round, pi, m, p, q);
-        Tc g = czero<Tc>();
+        const int slot = it * ng + gid;
+        const bool valid = slot < npairs;
+        int p = pr, q = qr;
+        if (iters > 1 && valid) rr_pair(round, slot, m, p, q);
+        R gx = 0, gy = 0;
+        V xr[EPP], xi[EPP], yr[EPP], yi[EPP];
         if (valid) {
-          for (int c = gl; c < n; c += gs) cfmac(g, X[p * ld + c], X[q * ld + c]);
+          const R* px = Xr + p * ldp + 2 * gl;
+          const R* pxi = Xi + p * ldp + 2 * gl;
+          const R* py = Xr + q * ldp + 2 * gl;
+          const R* pyi = Xi + q * ldp + 2 * gl;
+          V A = splat<V>((R)0), B = A, C = A, D = A;
+#pragma unroll
+          for (int e = 0; e < EPP; ++e) {
+            xr[e] = *reinterpret_cast<const V*>(px + 2 * gs * e);
+            xi[e] = *reinterpret_cast<const V*>(pxi + 2 * gs * e);
+            yr[e] = *reinterpret_cast<const V*>(py + 2 * gs * e);
+            yi[e] = *reinterpret_cast<const V*>(pyi + 2 * gs * e);
+            // x . conj(y) = (xr yr + xi yi) + i (xi yr - xr yi)
+            A = pfma(xr[e], yr[e], A);
+            B = pfma(xi[e], yi[e], B);
+            C = pfma(xi[e], yr[e], C);
+            D = pfma(xr[e], yi[e], D);
+          }
+          gx = (A.x + A.y) + (B.x + B.y);
+          gy = (C.x + C.y) - (D.x + D.y);
         }
         for (int o = gs >> 1; o; o >>= 1) {
-          g.x += __shfl_xor_sync(FULL, g.x, o);
-          g.y += __shfl_xor_sync(FULL, g.y, o);
+          gx += __shfl_xor_sync(FULL, gx, o);
+          gy += __shfl_xor_sync(FULL, gy, o);
         }
         if (valid) {
           const R alpha = nrm[p], beta = nrm[q];
-          const R ga = sqrt(g.x * g.x + g.y * g.y);
-          if (alpha > (R)0 && beta > (R)0 && ga > tol * sqrt(alpha) * sqrt(beta)) {
-            const R zeta = (beta - alpha) / (2 * ga);
-            const R az = fabs(zeta);
-            const R root = az > (R)1 ? az * sqrt((R)1 + (R)1 / (zeta * zeta)) : sqrt((R)1 + zeta * zeta);
-            const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (az + root);
-            const R cs = (R)1 / sqrt((R)1 + t * t);
-            const R sn = cs * t;
-            const R ex = g.x / ga, ey = g.y / ga;  // e^{i phi} = gamma / |gamma|
-            // x' = c x - s e^{i phi} y ; y' = s e^{-i phi} x + c y
-            for (int c = gl; c < n; c += gs) {
-              const Tc x = X[p * ld + c], y = X[q * ld + c];
-              Tc xn, yn;
-              xn.x = cs * x.x - sn * (ex * y.x - ey * y.y);
-              xn.y = cs * x.y - sn * (ex * y.y + ey * y.x);
-              yn.x = sn * (ex * x.x + ey * x.y) + cs * y.x;
-              yn.y = sn * (ex * x.y - ey * x.x) + cs * y.y;
-              X[p * ld + c] = xn;
-              X[q * ld + c] = yn;
+          R cs, sex, sey, tga;
+          if (rot_params(gx, gy, alpha, beta, tol, cs, sex, sey, tga)) {
+            const V CS = splat<V>(cs), SX = splat<V>(sex), SY = splat<V>(sey);
+            const V NSX = splat<V>(-sex), NSY = splat<V>(-sey);
+            R* px = Xr + p * ldp + 2 * gl;
+            R* pxi = Xi + p * ldp + 2 * gl;
+            R* py = Xr + q * ldp + 2 * gl;
+            R* pyi = Xi + q * ldp + 2 * gl;
+            // x' = c x - se y ; y' = conj(se) x + c y
+#pragma unroll
+            for (int e = 0; e < EPP; ++e) {
+              *reinterpret_cast<V*>(px + 2 * gs * e) = pfma(SY, yi[e], pfma(NSX, yr[e], pmul(CS, xr[e])));
+              *reinterpret_cast<V*>(pxi + 2 * gs * e) = pfma(NSY, yr[e], pfma(NSX, yi[e], pmul(CS, xi[e])));
+              *reinterpret_cast<V*>(py + 2 * gs * e) = pfma(SY, xi[e], pfma(SX, xr[e], pmul(CS, yr[e])));
+              *reinterpret_cast<V*>(pyi + 2 * gs * e) = pfma(NSY, xr[e], pfma(SX, xi[e], pmul(CS, yi[e])));
             }
             if (gl == 0) {
-              nrm[p] = alpha - t * ga;
-              nrm[q] = beta + t * ga;
-              *flag = 1;
-              atomicAdd(nrot, 1);
+              nrm[p] = alpha - tga;
+              nrm[q] = beta + tga;
+              ++my_rot;
+            }
+            any = 1;
+          }
+        }
+      }
+      if (pi0 == 0) {
+        pr = round + 1;
+      } else {
+        pr = pr + 1 == m - 1 ? 0 : pr + 1;
+        qr = qr + 1 == m - 1 ? 0 : qr + 1;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(any)) break;
+  }
+  if (gl == 0 && my_rot) atomicAdd(nrot, my_rot);
+  return sweep + 1;
+}
+
+// ---- block Jacobi with register-resident rows (single precision) -------------------------
+// The rows are grouped in blocks of four.  In a block round each warp holds a
+// pair of blocks (eight rows) in registers, lane l owning the element pairs at
+// columns 2l + 64j of each row, and makes every cross pair of the two blocks
+// orthogonal in four sub-rounds of four disjoint pairs (in the first block round
+// of a sweep also the six pairs inside each block, in three sub-rounds).  The
+// blocks meet in circle-method order, so a sweep still visits every row pair
+// once; only the block rounds need block-wide barriers.  The four inner products
+// of a sub-round are reduced across the warp together (a 9-shuffle
+// reduce-scatter); lanes 8k..8k+7 then compute the rotation of pair k and
+// broadcast it.
+template <int CPL>
+struct BJRows {
+  float2 r[8][CPL];  // real parts, element pairs
+  float2 i[8][CPL];  // imaginary parts
+  float nr[8];       // squared row norms (identical in every lane)
+};
+
+template <int CPL, int P0, int Q0, int P1, int Q1, int P2, int Q2, int P3, int Q3>
+__device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any, int& nrot) {
+  const int lane = threadIdx.x & 31;
+  float v[8];
+#define LT_BJ_DOT(K, P, Q)                                                   \
+  {                                                                         \
+    float2 A = make_float2(0.f, 0.f), B = A, C = A, D = A;                  \
+    _Pragma("unroll") for (int j = 0; j < CPL; ++j) {                       \
+      A = pfma(w.r[P][j], w.r[Q][j], A);                                    \
+      B = pfma(w.i[P][j], w.i[Q][j], B);                                    \
+      C = pfma(w.i[P][j], w.r[Q][j], C);                                    \
+      D = pfma(w.r[P][j], w.i[Q][j], D);                                    \
+    }                                                                       \
+    v[2 * K] = (A.x + A.y) + (B.x + B.y);                                   \
+    v[2 * K + 1] = (C.x + C.y) - (D.x + D.y);                               \
+  }
+  LT_BJ_DOT(0, P0, Q0)
+  LT_BJ_DOT(1, P1, Q1)
+  LT_BJ_DOT(2, P2, Q2)
+  LT_BJ_DOT(3, P3, Q3)
+#undef LT_BJ_DOT
+  // reduce-scatter: afterwards lane l holds value (l >> 2) summed over the warp
+  {
+    const bool hi = lane & 16;
+    float k4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float send = hi ? v[t] : v[4 + t];
+      const float keep = hi ? v[4 + t] : v[t];
+      k4[t] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+    const bool h8 = lane & 8;
+    float k2[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float send = h8 ? k4[t] : k4[2 + t];
+      const float keep = h8 ? k4[2 + t] : k4[t];
+      k2[t] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    const bool h4 = lane & 4;
+    float k1 = (h4 ? k2[1] : k2[0]) + __shfl_xor_sync(FULL, h4 ? k2[0] : k2[1], 4);
+    k1 += __shfl_xor_sync(FULL, k1, 2);
+    k1 += __shfl_xor_sync(FULL, k1, 1);
+    v[0] = k1;
+  }
+  // lanes 8k..8k+3 hold gx of pair k, lanes 8k+4..8k+7 its gy
+  const float other = __shfl_xor_sync(FULL, v[0], 4);
+  const float gx = (lane & 4) ? other : v[0];
+  const float gy = (lane & 4) ? v[0] : other;
+  const int k = lane >> 3;
+  const float alpha = k == 0 ? w.nr[P0] : k == 1 ? w.nr[P1] : k == 2 ? w.nr[P2] : w.nr[P3];
+  const float beta = k == 0 ? w.nr[Q0] : k == 1 ? w.nr[Q1] : k == 2 ? w.nr[Q2] : w.nr[Q3];
+  float cs = 1.f, sex = 0.f, sey = 0.f, tga = 0.f;
+  const int rot = rot_params(gx, gy, alpha, beta, tol, cs, sex, sey, tga) ? 1 : 0;
+  const unsigned rmask = __ballot_sync(FULL, rot);
+#define LT_BJ_ROT(K, P, Q)                                                    \
+  if (rmask & (1u << (8 * K))) {                                             \
+    const float c_ = __shfl_sync(FULL, cs, 8 * K);                           \
+    const float x_ = __shfl_sync(FULL, sex, 8 * K);                          \
+    const float y_ = __shfl_sync(FULL, sey, 8 * K);                          \
+    const float t_ = __shfl_sync(FULL, tga, 8 * K);                          \
+    const float2 CS = make_float2(c_, c_), SX = make_float2(x_, x_);         \
+    const float2 SY = make_float2(y_, y_), NSX = make_float2(-x_, -x_);      \
+    const float2 NSY = make_float2(-y_, -y_);                                \
+    _Pragma("unroll") for (int j = 0; j < CPL; ++j) {                        \
+      const float2 xr = w.r[P][j], xi = w.i[P][j], yr = w.r[Q][j], yi = w.i[Q][j]; \
+      w.r[P][j] = pfma(SY, yi, pfma(NSX, yr, pmul(CS, xr)));                 \
+      w.i[P][j] = pfma(NSY, yr, pfma(NSX, yi, pmul(CS, xi)));                \
+      w.r[Q][j] = pfma(SY, xi, pfma(SX, xr, pmul(CS, yr)));                  \
+      w.i[Q][j] = pfma(NSY, xr, pfma(SX, xi, pmul(CS, yi)));                 \
+    }                                                                        \
+    w.nr[P] -= t_;                                                           \
+    w.nr[Q] += t_;                                                           \
+    any = 1;                                                                 \
+    ++nrot;                                                                  \
+  }
+  LT_BJ_ROT(0, P0, Q0)
+  LT_BJ_ROT(1, P1, Q1)
+  LT_BJ_ROT(2, P2, Q2)
+  LT_BJ_ROT(3, P3, Q3)
+#undef LT_BJ_ROT
+}
+
+// Sweeps over the mp (multiple of 8, rows m..mp-1 zero) rows of the planar
+// matrix; returns the number of sweeps.  CPL element pairs per lane and row
+// cover npad = 64 CPL columns (lanes beyond npad hold zeros).
+template <int CPL>
+__device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int npad, float* nrm,
+                              int* nrot_out, int max_sweeps, double tol_override) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int NB = mp >> 2;  // even
+  const float tol = tol_override > 0.0 ? (float)tol_override : FLT_EPSILON * sqrtf((float)n);
+  int nrot = 0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    __syncthreads();
+    for (int r = warp; r < mp; r += nw) {
+      float acc = 0.f;
+      for (int c = lane; c < n; c += 32) {
+        const float u = Xr[r * ldp + c], v = Xi[r * ldp + c];
+        acc = fmaf(u, u, fmaf(v, v, acc));
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (lane == 0) nrm[r] = acc;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int br = 0; br < NB - 1; ++br) {
+      for (int bp = warp; bp < (NB >> 1); bp += nw) {
+        int A, B;
+        rr_pair(br, bp, NB, A, B);
+        BJRows<CPL> w;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
+          w.nr[t] = nrm[row];
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            const int c = 2 * lane + 64 * j;
+            if (c < npad) {
+              w.r[t][j] = *reinterpret_cast<const float2*>(Xr + row * ldp + c);
+              w.i[t][j] = *reinterpret_cast<const float2*>(Xi + row * ldp + c);
+            } else {
+              w.r[t][j] = make_float2(0.f, 0.f);
+              w.i[t][j] = make_float2(0.f, 0.f);
+            }
+          }
+        }
+        if (br == 0) {
+          // pairs inside each block: circle method on four rows
+          bj_subround<CPL, 0, 3, 1, 2, 4, 7, 5, 6>(w, tol, any, nrot);
+          bj_subround<CPL, 1, 3, 2, 0, 5, 7, 6, 4>(w, tol, any, nrot);
+          bj_subround<CPL, 2, 3, 0, 1, 6, 7, 4, 5>(w, tol, any, nrot);
+        }
+        bj_subround<CPL, 0, 4, 1, 5, 2, 6, 3, 7>(w, tol, any, nrot);
+        bj_subround<CPL, 0, 5, 1, 6, 2, 7, 3, 4>(w, tol, any, nrot);
+        bj_subround<CPL, 0, 6, 1, 7, 2, 4, 3, 5>(w, tol, any, nrot);
+        bj_subround<CPL, 0, 7, 1, 4, 2, 5, 3, 6>(w, tol, any, nrot);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
+          if (lane == 0) nrm[row] = w.nr[t];
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+            const int c = 2 * lane + 64 * j;
+            if (c < npad) {
+              *reinterpret_cast<float2*>(Xr + row * ldp + c) = w.r[t][j];
+              *reinterpret_cast<float2*>(Xi + row * ldp + c) = w.i[t][j];
             }
           }
         }
       }
       __syncthreads();
     }
-    const int rotated = *flag;
-    __syncthreads();
-    if (!rotated) break;
+    if (!__syncthreads_or(any)) break;
   }
+  if (lane == 0 && nrot) atomicAdd(nrot_out, nrot);
   return sweep + 1;
 }
 
+// launch shape per precision: 256 threads; the pair Jacobi holds 8 (single) or
+// 4 (double) element pairs of each row per lane
+template <typename R> struct BondShape;
+template <> struct BondShape<float> { static constexpr int NT = 256, EPP = 8; };
+template <> struct BondShape<double> { static constexpr int NT = 256, EPP = 4; };
+
 // ---- the two-site update -----------------------------------------------------------------
+// Workspace (shared memory, or per-CTA global scratch when it does not fit):
+// theta planar, 2 m (n+2) reals, then V_k^+ rows (k x (n+1) complex), whose
+// region first serves to stage B_{b+1} during theta formation.
 template <typename R>
-__global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
+__global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<R> a) {
   typedef typename CT<R>::T Tc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_sig[LT_MAX_DIM];
@@ -181,10 +513,11 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
   __shared__ int s_perm[LT_MAX_DIM];
   __shared__ Tc s_gate[16];
   __shared__ double s_lamL[LT_MAX_CHI];
-  __shared__ int s_flag, s_k, s_nrot;
+  __shared__ int s_k, s_nrot;
   __shared__ double s_norm, s_wdisc;
 
-  Tc* X = a.use_smem ? reinterpret_cast<Tc*>(smem_raw) : a.scratch + (long long)blockIdx.x * a.scratch_stride;
+  R* W = a.use_smem ? reinterpret_cast<R*>(smem_raw)
+                    : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
   const int L = a.L, chi = a.chi, tid = threadIdx.x;
   const long long ntask = (long long)(*a.n_trajs) * a.nb;
   for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
@@ -199,9 +532,18 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
     const int chiM = dm[b];
     const int chiR = b == L - 2 ? 1 : dm[b + 1];
     const int m = 2 * chiL, n = 2 * chiR, ld = n + 1;
+    // single precision, theta of at least 32 x 64: block Jacobi over rows padded
+    // to a multiple of 8 and columns padded to 64 or 128; otherwise pair Jacobi
+    const bool blocked = sizeof(R) == 4 && m >= 32 && n >= 64;
+    const int npad = blocked ? (n <= 64 ? 64 : 128)
+                             : 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(n);
+    const int mp = blocked ? (m + 7) & ~7 : m;
+    const int ldp = npad + 2;
     Tc* Bl = a.B + ((long long)traj * L + b) * a.slot;
     Tc* Br = Bl + a.slot;
-    Tc* Y = X + m * ld;
+    R* Xr = W;
+    R* Xi = W + mp * ldp;
+    Tc* Y = reinterpret_cast<Tc*>(W + 2 * mp * ldp);
     if (tid < 16) {
       if (a.gates) {
         const double2 g = a.gates[b * 16 + tid];
@@ -214,16 +556,28 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
       s_lamL[i] = b == 0 ? 1.0 : a.lam[((long long)traj * (L - 1) + b - 1) * chi + i];
     if (tid == 0) s_nrot = 0;
     __syncthreads();
-    form_theta<R>(X, ld, Bl, Br, chiL, chiM, chiR, s_gate, s_lamL, true);
-    const int sweeps = jacobi_rows<R>(X, ld, m, n, s_nrm, &s_flag, &s_nrot, a.max_sweeps, a.tol);
+    form_theta<R>(Xr, Xi, ldp, npad, mp, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
+    int sweeps;
+    if (blocked) {
+      if (npad == 64)
+        sweeps = jacobi_blocked<1>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
+                                   mp, n, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
+                                   a.max_sweeps, a.tol);
+      else
+        sweeps = jacobi_blocked<2>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
+                                   mp, n, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
+                                   a.max_sweeps, a.tol);
+    } else {
+      sweeps = jacobi_rows<R, BondShape<R>::EPP>(Xr, Xi, ldp, m, n, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+    }
     // singular values squared, accumulated in double
     {
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
       for (int r = warp; r < m; r += nw) {
         double acc = 0.0;
         for (int c = lane; c < n; c += 32) {
-          const Tc v = X[r * ld + c];
-          acc += (double)v.x * v.x + (double)v.y * v.y;
+          const double u = Xr[r * ldp + c], v = Xi[r * ldp + c];
+          acc += u * u + v * v;
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -282,21 +636,34 @@ __global__ void __launch_bounds__(LT_BLOCK) bond_update_kernel(BondArgs<R> a) {
       const int r = s_perm[j];
       const double sg = s_sig[r];
       const R inv = sg > 0.0 ? (R)(1.0 / sqrt(sg)) : (R)0;
-      Y[j * ld + c] = cscale(X[r * ld + c], inv);
+      Y[j * ld + c] = cmk<Tc>(Xr[r * ldp + c] * inv, Xi[r * ldp + c] * inv);
     }
     __syncthreads();
     // theta~ again (unweighted), then B_b' = theta~ V_k / ||S_k||
-    form_theta<R>(X, ld, Bl, Br, chiL, chiM, chiR, s_gate, s_lamL, false);
+    form_theta<R>(Xr, Xi, ldp, n, m, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL, false);
     __syncthreads();
     {
+      // four rows of theta~ per thread against one row of V_k^+; consecutive
+      // lanes take consecutive j
       const R invn = (R)(1.0 / s_norm);
-      for (int idx = tid; idx < m * k; idx += blockDim.x) {
-        const int r = idx / k, j = idx - r * k;
-        const Tc* xr = X + r * ld;
+      const int rq = (m + 3) >> 2;
+      for (int idx = tid; idx < rq * k; idx += blockDim.x) {
+        const int r0 = (idx / k) << 2, j = idx - (idx / k) * k;
         const Tc* yj = Y + j * ld;
-        Tc acc = czero<Tc>();
-        for (int c = 0; c < n; ++c) cfmac(acc, xr[c], yj[c]);
-        Bl[idx] = cscale(acc, invn);
+        Tc acc[4] = {czero<Tc>(), czero<Tc>(), czero<Tc>(), czero<Tc>()};
+        const int nr = m - r0 < 4 ? m - r0 : 4;
+        for (int c = 0; c < n; ++c) {
+          const Tc yv = yj[c];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (u < nr) {
+              const int o = (r0 + u) * ldp + c;
+              cfmac(acc[u], cmk<Tc>(Xr[o], Xi[o]), yv);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < nr) Bl[(r0 + u) * k + j] = cscale(acc[u], invn);
       }
       for (int idx = tid; idx < k * n; idx += blockDim.x) {
         const int j = idx / n, c = idx - j * n;
@@ -705,8 +1072,22 @@ inline int grid_for(long long n, int block) {
 
 // ---- launchers -------------------------------------------------------------------------------
 size_t bond_smem_bytes(int chi, size_t celt) {
+  // planar theta mp (npad+2) plus V_k^+ k (n+1), in complex elements: npad is n
+  // rounded up to the span of a pair-Jacobi lane group (2 EPP gs columns) or,
+  // for the single-precision block Jacobi, to 64 or 128; mp is m rounded up to 8
   const size_t m = 2 * (size_t)chi, n = 2 * (size_t)chi, k = chi;
-  return (m + k) * (n + 1) * celt;
+  const bool single = celt == sizeof(float2);
+  const size_t epp = single ? BondShape<float>::EPP : BondShape<double>::EPP;
+  size_t gs = 1;
+  while (gs * 2 * epp < n && gs < 32) gs <<= 1;
+  size_t npad = 2 * epp * gs;
+  size_t mp = m;
+  if (single) {
+    const size_t nb = n <= 64 ? 64 : 128;
+    npad = npad > nb ? npad : nb;
+    mp = (m + 7) & ~(size_t)7;
+  }
+  return (mp * (npad + 2) + k * (n + 1)) * celt;
 }
 
 size_t env_scratch_elems(int L, int chi) { return ((size_t)L + 1 + 7) * (size_t)chi * chi; }
@@ -738,7 +1119,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.tol = c->jacobi_tol;
   a.sweep_hist = c->sweep_hist;
   a.counters = c->counters;
-  bond_update_kernel<R><<<c->bond_grid, LT_BLOCK, c->bond_use_smem ? c->bond_smem : 0, c->stream>>>(a);
+  bond_update_kernel<R><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
 }
@@ -880,14 +1261,14 @@ cudaError_t configure_bond(lt_ctx_s* c) {
     e = cudaFuncSetAttribute(bond_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)c->bond_smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<float>, LT_BLOCK,
-                                                      c->bond_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<float>,
+                                                      BondShape<float>::NT, c->bond_smem);
   } else {
     e = cudaFuncSetAttribute(bond_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)c->bond_smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<double>, LT_BLOCK,
-                                                      c->bond_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<double>,
+                                                      BondShape<double>::NT, c->bond_smem);
   }
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
@@ -955,4 +1336,17 @@ extern "C" lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, in
   if (precision == LT_MIXED) env_kernel<float, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
   else env_kernel<double, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? LT_OK : LT_ERR_CUDA;
+}
+
+// resident environment CTAs: as many as fit on the device (their workspace
+// is global scratch), at most one per trajectory
+int env_grid(lt_ctx_s* c) {
+  int occ = 0;
+  cudaError_t e = c->prec == LT_MIXED
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_kernel<float>, LT_BLOCK, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_kernel<double>, LT_BLOCK, 0);
+  if (e != cudaSuccess || occ < 1) occ = 2;
+  if (occ > 8) occ = 8;
+  const long long g = (long long)occ * c->num_sms;
+  return (int)(g < c->n_traj ? g : c->n_traj);
 }
