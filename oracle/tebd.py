@@ -25,10 +25,14 @@ One time step of a trajectory (Sec. 4.1, after Eq. ErrorCLT's preceding text):
   (Eq. QJump1), the norm being restored by each bond's renormalisation.
 
 Canonical form after a jump: L_k changes only B_k (plus a sign on the occupied
-component of every B_j, j < k, for the fermionic string, a unitary).  Identity-gate
-bond updates at bonds k-1, ..., 1 (right to left) make B_k..B_1 right-canonical,
-then identity-gate updates at bonds 0, ..., L-2 (left to right) restore every
-Lambda as the exact Schmidt spectrum (Sec. 2.2, Eq. ShiftCenter, done by SVD).
+component of every B_j, j < k, for the fermionic string, a unitary).  One-site
+SVDs shift the orthogonality centre (Sec. 2.2, Eq. ShiftCenter): right to left
+over bonds L-2, ..., 0 each B_{b+1} is made right-canonical and its U S absorbed
+into B_b; then left to right over bonds 0, ..., L-2 the SVD of Lambda_{b-1} B_b
+restores Lambda_b as the exact Schmidt spectrum.  With B_{b+1} right-canonical
+this equals the two-site update with the identity gate.  The sweep covers the
+whole chain because the effective-Hamiltonian layers before the jump leave the
+form only approximately canonical.
 """
 import numpy as np
 
@@ -186,11 +190,56 @@ class Trajectory:
                 self.B[j][:, 1, :] *= -1.0
         self.recanonicalize(site)
 
-    def recanonicalize(self, site):
-        for b in range(site - 1, 0, -1):
-            self.update_bond(b, IDENTITY4)
+    def recanonicalize(self, site=None):
+        """Restore the exact canonical form (every B right-canonical, every Lambda
+        the Schmidt spectrum of its bond).  The sweep covers the whole chain: the
+        effective-Hamiltonian layers before a jump leave the form only
+        approximately canonical on both sides of the jump site."""
+        for b in range(self.cfg.L - 2, -1, -1):
+            self.shift_left(b)
         for b in range(0, self.cfg.L - 1):
-            self.update_bond(b, IDENTITY4)
+            self.restore_bond(b)
+
+    # ---- moving the orthogonality centre by one-site SVDs (Sec. 2.2, Eq. ShiftCenter)
+    def _keep(self, S):
+        k = int(np.count_nonzero(S > self.cfg.svd_cut * S[0]))
+        return max(1, min(self.cfg.chi_max, k))
+
+    def shift_left(self, b):
+        """Make B_{b+1} right-canonical: B_{b+1} = U S V^+ as a chi_b x (2 chi_{b+1})
+        matrix, B_{b+1} <- V_k^+, B_b <- B_b U_k S_k (the state is unchanged up to
+        the discarded singular values; no renormalisation)."""
+        Bl, Br = self.B[b], self.B[b + 1]
+        chiL, chiM, chiR = Bl.shape[0], Br.shape[0], Br.shape[2]
+        U, S, Vh = np.linalg.svd(Br.reshape(chiM, 2 * chiR), full_matrices=False)
+        if not S[0] > 0.0:
+            raise FloatingPointError("site tensor vanished at %d" % (b + 1))
+        k = min(self._keep(S), len(S))
+        self.B[b + 1] = Vh[:k].reshape(k, 2, chiR).copy()
+        self.B[b] = (Bl.reshape(2 * chiL, chiM) @ (U[:, :k] * S[:k])).reshape(chiL, 2, k)
+        self.lam[b] = S[:k] / np.sqrt(np.sum(S[:k] ** 2))
+
+    def restore_bond(self, b):
+        """With Lambda_{b-1} exact and B_{b+1}, B_{b+2}, ... right-canonical, the
+        SVD of Lambda_{b-1} B_b (a 2 chi_{b-1} x chi_b matrix) gives the Schmidt
+        values of bond b: Lambda_b <- S_k / ||S_k||, B_b <- B_b V_k / ||S_k||,
+        B_{b+1} <- V_k^+ B_{b+1}; the discarded weight is recorded."""
+        Bl, Br = self.B[b], self.B[b + 1]
+        chiL, chiM, chiR = Bl.shape[0], Bl.shape[2], Br.shape[2]
+        Bm = Bl.reshape(2 * chiL, chiM)
+        M = np.repeat(self.left_weight(b), 2)[:, None] * Bm
+        U, S, Vh = np.linalg.svd(M, full_matrices=False)
+        if not S[0] > 0.0:
+            raise FloatingPointError("site tensor vanished at %d" % b)
+        k = min(self._keep(S), len(S))
+        total = float(np.sum(S ** 2))
+        kept = float(np.sum(S[:k] ** 2))
+        norm = np.sqrt(kept)
+        self.trunc_weight += (total - kept) / total
+        Vk_h = Vh[:k]
+        self.B[b] = (Bm @ Vk_h.conj().T / norm).reshape(chiL, 2, k)
+        self.B[b + 1] = (Vk_h @ Br.reshape(chiM, 2 * chiR)).reshape(k, 2, chiR)
+        self.lam[b] = S[:k] / norm
 
     # ---- <c_i^+ c_j> by transfer matrices -------------------------------------
     def correlation(self):

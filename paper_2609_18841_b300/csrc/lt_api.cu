@@ -127,6 +127,8 @@ lt_status check_device_error(lt_ctx_s* c) {
   if (err & LT_EBIT_THETA_ZERO) return fail(c, LT_ERR_NUMERICAL, "bond update", "theta vanished");
   if (err & LT_EBIT_PROB)
     return fail(c, LT_ERR_NUMERICAL, "jump decision", "jump probability per step >= 0.5; reduce dt");
+  if (err & LT_EBIT_WORKSPACE)
+    return fail(c, LT_ERR_NUMERICAL, "bond update", "a task exceeded its workspace");
   if (err & LT_EBIT_BADARG) {
     c->last_error = "replayed channel out of range";
     int zero = 0;
@@ -373,10 +375,11 @@ lt_status lt_apply_jumps(lt_ctx c, int64_t step, const int32_t* replay, int32_t*
   LT_CK(launch_env(c, 1, step, replay ? c->replay : nullptr));
   LT_CK(launch_compact(c));
   LT_CK(launch_jump_apply(c));
-  // restore the canonical form of the jumped histories: right to left over
-  // bonds site-1 .. 1, then left to right over every bond (identity gate)
-  for (int b = c->L - 2; b >= 1; --b) LT_CK(launch_bond(c, c->jumped_list, c->counts + 1, b, 1, nullptr, 1));
-  for (int b = 0; b <= c->L - 2; ++b) LT_CK(launch_bond(c, c->jumped_list, c->counts + 1, b, 1, nullptr, 0));
+  // restore the canonical form of the jumped histories by one-site SVDs: right
+  // to left over every bond (B_{b+1} right-canonical), then left to right
+  // (Lambda_b the Schmidt spectrum)
+  for (int b = c->L - 2; b >= 0; --b) LT_CK(launch_bond(c, c->jumped_list, c->counts + 1, b, 1, nullptr, 1));
+  for (int b = 0; b <= c->L - 2; ++b) LT_CK(launch_bond(c, c->jumped_list, c->counts + 1, b, 1, nullptr, 2));
   if (replay) {
     st = check_device_error(c);
     if (st != LT_OK) return st;

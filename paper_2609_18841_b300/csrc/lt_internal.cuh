@@ -19,6 +19,7 @@
 #define LT_EBIT_PROB 2         // jump probability per step >= 0.5
 #define LT_EBIT_NOCONV 4       // Jacobi hit its sweep limit (recorded, not fatal)
 #define LT_EBIT_BADARG 8       // replayed channel out of range
+#define LT_EBIT_WORKSPACE 16   // a task did not fit its workspace (skipped)
 
 // ---- complex arithmetic on float2 / double2 ------------------------------------
 template <typename R> struct CT;
@@ -105,8 +106,8 @@ template <typename R> struct BondArgs {
   const int* n_trajs;
   int bond0, nb;
   const double2* gates;  // [L-1][16] or nullptr = identity
-  const int* channel;    // per-trajectory channel, used when rl_filter
-  int rl_filter;         // 1: apply only if bond0 <= site(channel) - 1
+  int mode;              // 0 two-site gate update, 1 shift left, 2 restore bond
+  long long ws_elems;    // workspace capacity in complex elements
   int L, chi, slot;
   double cut;
   int* err;
@@ -201,7 +202,7 @@ struct lt_ctx_s {
 
 // ---- kernel launchers (lt_kernels.cu) ----------------------------------------------
 cudaError_t launch_bond(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0, int nb,
-                        const double2* gates, int rl_filter);
+                        const double2* gates, int mode);
 cudaError_t launch_env(lt_ctx_s* c, int decide, long long step, const int* replay);
 cudaError_t launch_jump_apply(lt_ctx_s* c);
 cudaError_t launch_compact(lt_ctx_s* c);

@@ -500,10 +500,27 @@ template <typename R> struct BondShape;
 template <> struct BondShape<float> { static constexpr int NT = 256, EPP = 8; };
 template <> struct BondShape<double> { static constexpr int NT = 256, EPP = 4; };
 
-// ---- the two-site update -----------------------------------------------------------------
+// ---- the two-site update and the one-site canonical-form steps -----------------------------
+// mode 0: two-site update with the layer's gate (Eq. Theta): theta = Lambda_{b-1}
+//         G (B_b B_{b+1}), SVD, keep k, Lambda_b = S_k/|S_k|, B_{b+1} = V_k^+,
+//         B_b = theta~ V_k / |S_k|.
+// mode 1: shift the orthogonality centre left across bond b (Eq. ShiftCenter by
+//         a one-site SVD): B_{b+1} = U S V^+ (chi_b x 2chi_{b+1}), B_{b+1} = V_k^+,
+//         B_b = B_b B_{b+1} V_k (= B_b U_k S_k), no renormalisation.
+// mode 2: restore bond b: Lambda_{b-1} B_b = U S V^+ (2chi_{b-1} x chi_b),
+//         Lambda_b = S_k/|S_k|, B_b = B_b V_k / |S_k|, B_{b+1} = V_k^+ B_{b+1}.
 // Workspace (shared memory, or per-CTA global scratch when it does not fit):
-// theta planar, 2 m (n+2) reals, then V_k^+ rows (k x (n+1) complex), whose
-// region first serves to stage B_{b+1} during theta formation.
+// the Jacobi matrix planar (2 mcap ldp reals; in mode 0/1 later theta~), then
+// V_k^+ rows (k x (nJ+1) complex); in mode 0 the region after theta first
+// stages B_{b+1}, in mode 2 the region after V_k^+ stages the new site tensors.
+template <typename R>
+__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
+  blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64;
+  npad = blocked ? (nJ <= 64 ? 64 : 128)
+                 : 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(nJ);
+  mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
+}
+
 template <typename R>
 __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<R> a) {
   typedef typename CT<R>::T Tc;
@@ -518,32 +535,40 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
 
   R* W = a.use_smem ? reinterpret_cast<R*>(smem_raw)
                     : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
-  const int L = a.L, chi = a.chi, tid = threadIdx.x;
+  const int L = a.L, chi = a.chi, tid = threadIdx.x, mode = a.mode;
   const long long ntask = (long long)(*a.n_trajs) * a.nb;
   for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
     const int traj = a.trajs[task / a.nb];
     const int b = a.bond0 + 2 * (int)(task % a.nb);
-    if (a.rl_filter) {
-      const int site = a.channel[traj] / 3;
-      if (!(b <= site - 1)) continue;
-    }
     const int* dm = a.dims + (long long)traj * (L - 1);
     const int chiL = b == 0 ? 1 : dm[b - 1];
     const int chiM = dm[b];
     const int chiR = b == L - 2 ? 1 : dm[b + 1];
-    const int m = 2 * chiL, n = 2 * chiR, ld = n + 1;
-    // single precision, theta of at least 32 x 64: block Jacobi over rows padded
-    // to a multiple of 8 and columns padded to 64 or 128; otherwise pair Jacobi
-    const bool blocked = sizeof(R) == 4 && m >= 32 && n >= 64;
-    const int npad = blocked ? (n <= 64 ? 64 : 128)
-                             : 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(n);
-    const int mp = blocked ? (m + 7) & ~7 : m;
-    const int ldp = npad + 2;
+    // the matrix the Jacobi sweeps act on: mJ rows of length nJ
+    const int mJ = mode == 1 ? chiM : 2 * chiL;
+    const int nJ = mode == 2 ? chiM : 2 * chiR;
+    bool blocked;
+    int npad, mpJ;
+    jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ);
+    const int mcap = mode == 1 ? (mpJ > 2 * chiL ? mpJ : 2 * chiL) : mpJ;
+    const int ldp = npad + 2, ld = nJ + 1;
+    const int kmax = mJ < nJ ? (mJ < chi ? mJ : chi) : (nJ < chi ? nJ : chi);
+    // workspace check (complex elements); a task that would overrun is skipped
+    const long long vrows = (long long)kmax * ld;          // V_k^+
+    const long long stage0 = (long long)chiM * 2 * chiR;   // B_{b+1} staged in V_k^+'s place
+    const long long stage2 = (long long)kmax * (chiL > chiR ? 2 * chiL : 2 * chiR);
+    const long long need = (long long)mcap * ldp +
+                           (mode == 0 ? (vrows > stage0 ? vrows : stage0)
+                                      : vrows + (mode == 2 ? stage2 : 0));
+    if (need > a.ws_elems) {
+      if (tid == 0) atomicOr(a.err, LT_EBIT_WORKSPACE);
+      continue;
+    }
     Tc* Bl = a.B + ((long long)traj * L + b) * a.slot;
     Tc* Br = Bl + a.slot;
     R* Xr = W;
-    R* Xi = W + mp * ldp;
-    Tc* Y = reinterpret_cast<Tc*>(W + 2 * mp * ldp);
+    R* Xi = W + mcap * ldp;
+    Tc* Y = reinterpret_cast<Tc*>(W + 2 * mcap * ldp);
     if (tid < 16) {
       if (a.gates) {
         const double2 g = a.gates[b * 16 + tid];
@@ -556,26 +581,40 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
       s_lamL[i] = b == 0 ? 1.0 : a.lam[((long long)traj * (L - 1) + b - 1) * chi + i];
     if (tid == 0) s_nrot = 0;
     __syncthreads();
-    form_theta<R>(Xr, Xi, ldp, npad, mp, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
+    if (mode == 0) {
+      form_theta<R>(Xr, Xi, ldp, npad, mpJ, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
+    } else {
+      // one-site matrix, zero-padded to mpJ x npad
+      for (int i = tid; i < mpJ * npad; i += blockDim.x) {
+        const int r = i / npad, c = i - r * npad;
+        Tc v = czero<Tc>();
+        if (r < mJ && c < nJ) {
+          if (mode == 1) v = Br[r * nJ + c];
+          else v = cscale(Bl[r * nJ + c], (R)s_lamL[r >> 1]);
+        }
+        Xr[r * ldp + c] = v.x;
+        Xi[r * ldp + c] = v.y;
+      }
+    }
     int sweeps;
     if (blocked) {
       if (npad == 64)
         sweeps = jacobi_blocked<1>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
-                                   mp, n, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
+                                   mpJ, nJ, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
       else
         sweeps = jacobi_blocked<2>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
-                                   mp, n, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
+                                   mpJ, nJ, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
     } else {
-      sweeps = jacobi_rows<R, BondShape<R>::EPP>(Xr, Xi, ldp, m, n, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+      sweeps = jacobi_rows<R, BondShape<R>::EPP>(Xr, Xi, ldp, mpJ, nJ, s_nrm, &s_nrot, a.max_sweeps, a.tol);
     }
     // singular values squared, accumulated in double
     {
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-      for (int r = warp; r < m; r += nw) {
+      for (int r = warp; r < mJ; r += nw) {
         double acc = 0.0;
-        for (int c = lane; c < n; c += 32) {
+        for (int c = lane; c < nJ; c += 32) {
           const double u = Xr[r * ldp + c], v = Xi[r * ldp + c];
           acc += u * u + v * v;
         }
@@ -585,10 +624,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
       }
     }
     __syncthreads();
-    for (int r = tid; r < m; r += blockDim.x) {
+    for (int r = tid; r < mJ; r += blockDim.x) {
       const double v = s_sig[r];
       int rank = 0;
-      for (int j = 0; j < m; ++j) {
+      for (int j = 0; j < mJ; ++j) {
         const double u = s_sig[j];
         rank += (u > v) || (u == v && j < r);
       }
@@ -597,12 +636,12 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     __syncthreads();
     if (tid == 0) {
       double total = 0.0;
-      for (int j = 0; j < m; ++j) total += s_sig[j];
+      for (int j = 0; j < mJ; ++j) total += s_sig[j];
       const double s0 = s_sig[s_perm[0]];
       int k = 0;
       if (s0 > 0.0) {
         const double thr = a.cut * sqrt(s0);
-        while (k < m && k < n && k < chi && sqrt(s_sig[s_perm[k]]) > thr) ++k;
+        while (k < kmax && sqrt(s_sig[s_perm[k]]) > thr) ++k;
       } else {
         atomicOr(a.err, LT_EBIT_THETA_ZERO);
       }
@@ -614,12 +653,16 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
       s_wdisc = total > 0.0 ? (total - kept) / total : 0.0;
       if (a.sweep_hist) atomicAdd(a.sweep_hist + (sweeps < 63 ? sweeps : 63), 1);
       if (a.counters) {
-        // algorithmic real flops: theta (once) + Jacobi (row norms, one complex
-        // dot per pair per sweep, 24n per applied rotation, final norms) + split
-        const double dm_ = m, dn_ = n;
+        // algorithmic real flops: the Jacobi (row norms each sweep and at the end,
+        // one complex inner product per pair per sweep, 24 nJ per applied
+        // rotation) plus the contractions of the mode (theta formed once)
+        const double dm_ = mJ, dn_ = nJ;
         const double pairs = 0.5 * dm_ * (dm_ - 1.0) * sweeps;
-        const double fl = 8.0 * dm_ * dn_ * (chiM + 4) + 4.0 * dm_ * dn_ * (sweeps + 1) +
-                          8.0 * dn_ * pairs + 24.0 * dn_ * s_nrot + 8.0 * dm_ * k * dn_;
+        double fl = 4.0 * dm_ * dn_ * (sweeps + 1) + 8.0 * dn_ * pairs + 24.0 * dn_ * s_nrot;
+        const double mL = 2.0 * chiL, nR = 2.0 * chiR;
+        if (mode == 0) fl += 8.0 * mL * nR * (chiM + 4) + 8.0 * mL * k * nR;
+        else if (mode == 1) fl += 8.0 * mL * nR * chiM + 8.0 * mL * k * nR;
+        else fl += 8.0 * mL * chiM * k + 8.0 * k * chiM * nR;
         atomicAdd(a.counters + 0, 1ull);
         atomicAdd(a.counters + 1, (unsigned long long)s_nrot);
         atomicAdd(a.counters + 2, (unsigned long long)pairs);
@@ -631,28 +674,28 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     __syncthreads();
     const int k = s_k;
     // V_k^+ rows: Y[j] = X[perm j] / sigma_j
-    for (int idx = tid; idx < k * n; idx += blockDim.x) {
-      const int j = idx / n, c = idx - j * n;
+    for (int idx = tid; idx < k * nJ; idx += blockDim.x) {
+      const int j = idx / nJ, c = idx - j * nJ;
       const int r = s_perm[j];
       const double sg = s_sig[r];
       const R inv = sg > 0.0 ? (R)(1.0 / sqrt(sg)) : (R)0;
       Y[j * ld + c] = cmk<Tc>(Xr[r * ldp + c] * inv, Xi[r * ldp + c] * inv);
     }
     __syncthreads();
-    // theta~ again (unweighted), then B_b' = theta~ V_k / ||S_k||
-    form_theta<R>(Xr, Xi, ldp, n, m, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL, false);
-    __syncthreads();
-    {
-      // four rows of theta~ per thread against one row of V_k^+; consecutive
-      // lanes take consecutive j
-      const R invn = (R)(1.0 / s_norm);
+    if (mode != 2) {
+      // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
+      // B_b <- theta~ V_k (/ |S_k| in mode 0), B_{b+1} <- V_k^+
+      form_theta<R>(Xr, Xi, ldp, nJ, 2 * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL, false);
+      __syncthreads();
+      const int m = 2 * chiL;
+      const R invn = mode == 0 ? (R)(1.0 / s_norm) : (R)1;
       const int rq = (m + 3) >> 2;
       for (int idx = tid; idx < rq * k; idx += blockDim.x) {
         const int r0 = (idx / k) << 2, j = idx - (idx / k) * k;
         const Tc* yj = Y + j * ld;
         Tc acc[4] = {czero<Tc>(), czero<Tc>(), czero<Tc>(), czero<Tc>()};
         const int nr = m - r0 < 4 ? m - r0 : 4;
-        for (int c = 0; c < n; ++c) {
+        for (int c = 0; c < nJ; ++c) {
           const Tc yv = yj[c];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
@@ -665,15 +708,43 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
         for (int u = 0; u < 4; ++u)
           if (u < nr) Bl[(r0 + u) * k + j] = cscale(acc[u], invn);
       }
-      for (int idx = tid; idx < k * n; idx += blockDim.x) {
-        const int j = idx / n, c = idx - j * n;
+      for (int idx = tid; idx < k * nJ; idx += blockDim.x) {
+        const int j = idx / nJ, c = idx - j * nJ;
         Br[idx] = Y[j * ld + c];
       }
+    } else {
+      // B_b <- B_b V_k / |S_k| (2chi_{b-1} x k), staged, then written
+      Tc* St = Y + k * ld;
+      const int m = 2 * chiL, nR = 2 * chiR;
+      const R invn = (R)(1.0 / s_norm);
+      for (int idx = tid; idx < m * k; idx += blockDim.x) {
+        const int r = idx / k, j = idx - r * k;
+        const Tc* yj = Y + j * ld;
+        const Tc* br = Bl + r * chiM;
+        Tc acc = czero<Tc>();
+        for (int c = 0; c < chiM; ++c) cfmac(acc, br[c], yj[c]);
+        St[idx] = cscale(acc, invn);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < m * k; idx += blockDim.x) Bl[idx] = St[idx];
+      __syncthreads();
+      // B_{b+1} <- V_k^+ B_{b+1} (k x 2chi_{b+1}), staged, then written
+      for (int idx = tid; idx < k * nR; idx += blockDim.x) {
+        const int j = idx / nR, x = idx - j * nR;
+        const Tc* yj = Y + j * ld;
+        Tc acc = czero<Tc>();
+        for (int c = 0; c < chiM; ++c) cfma(acc, yj[c], Br[c * nR + x]);
+        St[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < k * nR; idx += blockDim.x) Br[idx] = St[idx];
+    }
+    {
       double* lb = a.lam + ((long long)traj * (L - 1) + b) * chi;
       for (int j = tid; j < k; j += blockDim.x) lb[j] = sqrt(s_sig[s_perm[j]]) / s_norm;
       if (tid == 0) {
         a.dims[(long long)traj * (L - 1) + b] = k;
-        a.trunc[(long long)traj * (L - 1) + b] += s_wdisc;
+        if (mode != 1) a.trunc[(long long)traj * (L - 1) + b] += s_wdisc;
       }
     }
     __syncthreads();
@@ -1072,29 +1143,40 @@ inline int grid_for(long long n, int block) {
 
 // ---- launchers -------------------------------------------------------------------------------
 size_t bond_smem_bytes(int chi, size_t celt) {
-  // planar theta mp (npad+2) plus V_k^+ k (n+1), in complex elements: npad is n
-  // rounded up to the span of a pair-Jacobi lane group (2 EPP gs columns) or,
-  // for the single-precision block Jacobi, to 64 or 128; mp is m rounded up to 8
-  const size_t m = 2 * (size_t)chi, n = 2 * (size_t)chi, k = chi;
+  // Largest workspace of a task, in complex elements, over the three modes with
+  // every dimension at chi (mirrors the layout of bond_update_kernel): the
+  // Jacobi matrix planar mcap x (npad + 2), V_k^+ k x (nJ + 1), plus the staging
+  // of B_{b+1} (mode 0) or of the new site tensors (mode 2).
   const bool single = celt == sizeof(float2);
   const size_t epp = single ? BondShape<float>::EPP : BondShape<double>::EPP;
-  size_t gs = 1;
-  while (gs * 2 * epp < n && gs < 32) gs <<= 1;
-  size_t npad = 2 * epp * gs;
-  size_t mp = m;
-  if (single) {
-    const size_t nb = n <= 64 ? 64 : 128;
-    npad = npad > nb ? npad : nb;
-    mp = (m + 7) & ~(size_t)7;
-  }
-  return (mp * (npad + 2) + k * (n + 1)) * celt;
+  auto npad_of = [&](size_t m, size_t n) {
+    size_t gs = 1;
+    while (gs * 2 * epp < n && gs < 32) gs <<= 1;
+    const bool blk = single && m >= 32 && n >= 64;
+    return blk ? (n <= 64 ? (size_t)64 : (size_t)128) : 2 * epp * gs;
+  };
+  auto mp_of = [&](size_t m, size_t n) {
+    return (single && m >= 32 && n >= 64) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
+  };
+  const size_t c2 = 2 * (size_t)chi, c1 = chi;
+  // mode 0: theta 2chi x 2chi, V^+ chi x (2chi+1), B_{b+1} staged in V^+'s region
+  const size_t need0 = mp_of(c2, c2) * (npad_of(c2, c2) + 2) +
+                       (c1 * (c2 + 1) > c1 * c2 ? c1 * (c2 + 1) : c1 * c2);
+  // mode 1: B_{b+1} chi x 2chi, later theta~ 2chi x 2chi in the same planes
+  const size_t mcap1 = mp_of(c1, c2) > c2 ? mp_of(c1, c2) : c2;
+  const size_t need1 = mcap1 * (npad_of(c1, c2) + 2) + c1 * (c2 + 1);
+  // mode 2: Lambda B_b 2chi x chi, V^+ chi x (chi+1), staged tensors chi x 2chi
+  const size_t need2 = mp_of(c2, c1) * (npad_of(c2, c1) + 2) + c1 * (c1 + 1) + c1 * c2;
+  size_t need = need0 > need1 ? need0 : need1;
+  need = need > need2 ? need : need2;
+  return need * celt;
 }
 
 size_t env_scratch_elems(int L, int chi) { return ((size_t)L + 1 + 7) * (size_t)chi * chi; }
 
 template <typename R>
 static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0,
-                                 int nb, const double2* gates, int rl_filter) {
+                                 int nb, const double2* gates, int mode) {
   BondArgs<R> a;
   a.B = reinterpret_cast<typename CT<R>::T*>(c->B);
   a.lam = c->lam;
@@ -1105,8 +1187,8 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.bond0 = bond0;
   a.nb = nb;
   a.gates = gates;
-  a.channel = c->channel;
-  a.rl_filter = rl_filter;
+  a.mode = mode;
+  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt) / c->celt);
   a.L = c->L;
   a.chi = c->chi;
   a.slot = c->slot;
@@ -1125,9 +1207,9 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
 }
 
 cudaError_t launch_bond(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0, int nb,
-                        const double2* gates, int rl_filter) {
-  if (c->prec == LT_MIXED) return launch_bond_t<float>(c, trajs, n_trajs, bond0, nb, gates, rl_filter);
-  return launch_bond_t<double>(c, trajs, n_trajs, bond0, nb, gates, rl_filter);
+                        const double2* gates, int mode) {
+  if (c->prec == LT_MIXED) return launch_bond_t<float>(c, trajs, n_trajs, bond0, nb, gates, mode);
+  return launch_bond_t<double>(c, trajs, n_trajs, bond0, nb, gates, mode);
 }
 
 static EnvArgs env_args(lt_ctx_s* c) {

@@ -227,3 +227,36 @@ def test_ensemble_matches_exact_correlation_within_clt_error():
     exact = np.real(np.diag(dense.corr_uniform_loss(L, 1.0, g, np.diag(occ).astype(complex),
                                                      n_steps * dt)))
     assert np.all(np.abs(mean - exact) < 4.5 * sem + 2e-3)
+
+
+def test_one_site_recanonicalisation_equals_two_site_identity_sweep():
+    # After a jump, shifting the orthogonality centre with one-site SVDs must give
+    # the same Schmidt spectra (gauge invariant) as two-site identity-gate updates
+    # over the whole chain; afterwards every B is right-canonical.
+    L, chi = 10, 32
+    cfg = tebd.TrajectoryConfig(L, dt=0.05, chi_max=chi, svd_cut=1e-13, gamma_loss=0.3,
+                                occupation=workloads.occupation(L, "neel"), seed=2)
+    tr = tebd.Trajectory(cfg)
+    g = tebd.StepGates(cfg)
+    for s in range(12):
+        tebd.step_trajectory(tr, g, 0, s, replay=-1)
+    for site in (0, 4, L - 1):
+        a = tebd.Trajectory.from_tensors(cfg, tr.B, tr.lam)
+        b = tebd.Trajectory.from_tensors(cfg, tr.B, tr.lam)
+        a.apply_jump(3 * site)                      # one-site sweep
+        O = model.jump_operator(model.LOSS)
+        b.B[site] = np.einsum('uv,avc->auc', O, b.B[site])
+        for j in range(site):
+            b.B[j] = b.B[j].copy()
+            b.B[j][:, 1, :] *= -1.0
+        for bond in range(L - 2, 0, -1):
+            b.update_bond(bond, tebd.IDENTITY4)
+        for bond in range(L - 1):
+            b.update_bond(bond, tebd.IDENTITY4)
+        assert a.bond_dims() == b.bond_dims()
+        for la, lb in zip(a.lam, b.lam):
+            assert np.abs(la - lb).max() < 1e-12
+        assert np.abs(a.correlation() - b.correlation()).max() < 1e-12
+        for Bi in a.B[1:]:
+            M = Bi.reshape(Bi.shape[0], -1)
+            assert np.abs(M @ M.conj().T - np.eye(M.shape[0])).max() < 1e-12
