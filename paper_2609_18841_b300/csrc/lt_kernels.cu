@@ -820,6 +820,38 @@ __device__ double right_envs(const typename CT<R>::T* B, const int* dm, int L, i
   return (double)Rl[0].x;
 }
 
+// Jump-or-evolve decision of one trajectory (Sec. 4.1): P = sum_k W_k dt over
+// the rates just written; draw r from Philox (counter traj_offset + traj, step,
+// purpose 0); jump iff r < P, to the least channel whose cumulative W dt
+// exceeds r.  Replayed channels bypass the draw.
+__device__ void decide_channel(const EnvArgs& a, int traj) {
+  const int L = a.L;
+  const double* rt = a.rates + (long long)traj * 3 * L;
+  int ch = -1;
+  const int rep = a.replay ? a.replay[traj] : -2;
+  if (rep == -2) {
+    double total = 0.0;
+    for (int j = 0; j < 3 * L; ++j) total += rt[j] * a.dt;
+    if (total >= 0.5) atomicOr(a.err, LT_EBIT_PROB);
+    const double r = philox_uniform(a.seed, (uint32_t)(a.traj_offset + traj), (uint64_t)a.step, 0u);
+    if (r < total) {
+      double cs = 0.0;
+      for (int j = 0; j < 3 * L; ++j) {
+        cs += rt[j] * a.dt;
+        if (cs > r) {
+          ch = j;
+          break;
+        }
+      }
+    }
+  } else if (rep >= 0) {
+    if (rep < 3 * L) ch = rep;
+    else atomicOr(a.err, LT_EBIT_BADARG);
+  }
+  a.channel[traj] = ch;
+  a.evolve[traj] = ch < 0 ? 1 : 0;
+}
+
 // env_kernel: per trajectory, exact <n_k> for every site, rates and decision
 // (kRates = false: densities only).
 template <typename R, bool kRates = true>
@@ -867,32 +899,178 @@ __global__ void __launch_bounds__(LT_BLOCK) env_kernel(EnvArgs a) {
       Le = Ln;
       Ln = tmp;
     }
-    if (kRates && a.decide && threadIdx.x == 0) {
-      const double* rt = a.rates + (long long)traj * 3 * L;
-      int ch = -1;
-      const int rep = a.replay ? a.replay[traj] : -2;
-      if (rep == -2) {
-        double total = 0.0;
-        for (int j = 0; j < 3 * L; ++j) total += rt[j] * a.dt;
-        if (total >= 0.5) atomicOr(a.err, LT_EBIT_PROB);
-        const double r = philox_uniform(a.seed, (uint32_t)(a.traj_offset + traj), (uint64_t)a.step, 0u);
-        if (r < total) {
-          double cs = 0.0;
-          for (int j = 0; j < 3 * L; ++j) {
-            cs += rt[j] * a.dt;
-            if (cs > r) {
-              ch = j;
-              break;
-            }
+    if (kRates && a.decide && threadIdx.x == 0) decide_channel(a, traj);
+    __syncthreads();
+  }
+}
+
+// ---- shared-memory tiled complex GEMM (one CTA of 256 threads) -----------------------
+// C (M x N) = (acc ? C : 0) + op(A) op(B), where op(A)(i,k) = A[i ar + k ac] and
+// op(B)(k,j) = B[k br + j bc], each conjugated when its flag is set.  Output
+// tiles of 64 x 64, each thread holding a 4 x 4 block; K in chunks of 16 staged
+// in shared memory (pitch 65, odd, so 8-byte accesses are conflict-free), with
+// the staging loop running along whichever operand stride is unit.
+#define LT_TG_P 65
+template <typename R>
+__device__ void tile_gemm(int M, int N, int K, const typename CT<R>::T* A, int ar, int ac,
+                          bool conjA, const typename CT<R>::T* B, int br, int bc, bool conjB,
+                          typename CT<R>::T* C, int ldc, bool acc, typename CT<R>::T* sA,
+                          typename CT<R>::T* sB) {
+  typedef typename CT<R>::T Tc;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int i0 = 0; i0 < M; i0 += 64) {
+    for (int j0 = 0; j0 < N; j0 += 64) {
+      Tc c[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) c[u][v] = czero<Tc>();
+      for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+          int ii, kk;
+          if (ac == 1) {
+            kk = e & 15;
+            ii = e >> 4;
+          } else {
+            ii = e & 63;
+            kk = e >> 6;
           }
+          const int gi = i0 + ii, gk = k0 + kk;
+          Tc v = czero<Tc>();
+          if (gi < M && gk < K) {
+            v = A[(long long)gi * ar + (long long)gk * ac];
+            if (conjA) v.y = -v.y;
+          }
+          sA[kk * LT_TG_P + ii] = v;
+          int jj, kb;
+          if (bc == 1) {
+            jj = e & 63;
+            kb = e >> 6;
+          } else {
+            kb = e & 15;
+            jj = e >> 4;
+          }
+          const int gj = j0 + jj, gkb = k0 + kb;
+          Tc w = czero<Tc>();
+          if (gkb < K && gj < N) {
+            w = B[(long long)gkb * br + (long long)gj * bc];
+            if (conjB) w.y = -w.y;
+          }
+          sB[kb * LT_TG_P + jj] = w;
         }
-      } else if (rep >= 0) {
-        if (rep < 3 * L) ch = rep;
-        else atomicOr(a.err, LT_EBIT_BADARG);
+        __syncthreads();
+        const int kn = K - k0 < 16 ? K - k0 : 16;
+        for (int kk = 0; kk < kn; ++kk) {
+          Tc av[4], bv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) av[u] = sA[kk * LT_TG_P + ty + 16 * u];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) bv[v] = sB[kk * LT_TG_P + tx + 16 * v];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) cfma(c[u][v], av[u], bv[v]);
+        }
+        __syncthreads();
       }
-      a.channel[traj] = ch;
-      a.evolve[traj] = ch < 0 ? 1 : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int gi = i0 + ty + 16 * u;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int gj = j0 + tx + 16 * v;
+          if (gj >= N) continue;
+          Tc o = c[u][v];
+          if (acc) {
+            const Tc p = C[(long long)gi * ldc + gj];
+            o.x += p.x;
+            o.y += p.y;
+          }
+          C[(long long)gi * ldc + gj] = o;
+        }
+      }
     }
+  }
+  __syncthreads();
+}
+
+// Right environments by tiled GEMMs: T'[(a,s)][b'] = sum_b B[(a,s)][b] R_{i+1}[b][b'],
+// R_i[a][a'] = sum_{(s,b')} T'[a][(s,b')] conj(B[a'][(s,b')]).  Returns <psi|psi>.
+template <typename R>
+__device__ double right_envs_tiled(const typename CT<R>::T* B, const int* dm, int L, int chi,
+                                   int slot, typename CT<R>::T* Rl, typename CT<R>::T* T,
+                                   typename CT<R>::T* sA, typename CT<R>::T* sB) {
+  typedef typename CT<R>::T Tc;
+  const int chi2 = chi * chi;
+  if (threadIdx.x == 0) Rl[(long long)L * chi2] = cmk<Tc>(1.0, 0.0);
+  __syncthreads();
+  for (int i = L - 1; i >= 0; --i) {
+    const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+    const Tc* Bi = B + (long long)i * slot;
+    const Tc* Rn = Rl + (long long)(i + 1) * chi2;
+    Tc* Ri = Rl + (long long)i * chi2;
+    tile_gemm<R>(2 * cl, cr, cr, Bi, cr, 1, false, Rn, chi, 1, false, T, cr, false, sA, sB);
+    tile_gemm<R>(cl, cl, 2 * cr, T, 2 * cr, 1, false, Bi, 1, 2 * cr, true, Ri, chi, false, sA, sB);
+  }
+  return (double)Rl[0].x;
+}
+
+// env kernel with tiled contractions: per trajectory exact <n_k> for every
+// site, then (kRates) rates and the Philox decision as in env_kernel
+template <typename R, bool kRates = true>
+__global__ void __launch_bounds__(LT_BLOCK) env_tiled_kernel(EnvArgs a) {
+  typedef typename CT<R>::T Tc;
+  __shared__ double red[32];
+  __shared__ Tc sA[16 * LT_TG_P], sB[16 * LT_TG_P];
+  const int L = a.L, chi = a.chi, chi2 = chi * chi;
+  Tc* ws = reinterpret_cast<Tc*>(a.scratch) + (long long)blockIdx.x * a.scratch_stride;
+  Tc* Rl = ws;                                  // (L+1) chi^2
+  Tc* T = Rl + (long long)(L + 1) * chi2;       // 2 chi^2
+  Tc* Le = T + 2 * chi2;                        // chi^2
+  Tc* Ln = Le + chi2;                           // chi^2
+  Tc* Mb = Ln + chi2;                           // 2 chi^2
+  Tc* N1 = T;                                   // reuses T in the left sweep
+  for (int traj = blockIdx.x; traj < a.n_traj; traj += gridDim.x) {
+    const Tc* B = reinterpret_cast<const Tc*>(a.B) + (long long)traj * L * a.slot;
+    const int* dm = a.dims + (long long)traj * (L - 1);
+    const double nrm2 = right_envs_tiled<R>(B, dm, L, chi, a.slot, Rl, T, sA, sB);
+    if (threadIdx.x == 0) Le[0] = cmk<Tc>(1.0, 0.0);
+    __syncthreads();
+    for (int k = 0; k < L; ++k) {
+      const int cl = k == 0 ? 1 : dm[k - 1], cr = k == L - 1 ? 1 : dm[k];
+      const Tc* Bk = B + (long long)k * a.slot;
+      const Tc* Rn = Rl + (long long)(k + 1) * chi2;
+      // M[a][(s,b)] = sum_a' Le[a][a'] B[a'][(s,b)]
+      tile_gemm<R>(cl, 2 * cr, cl, Le, chi, 1, false, Bk, 2 * cr, 1, false, Mb, 2 * cr, false, sA, sB);
+      // N1[a][b'] = sum_b M[a][(1,b)] R_{k+1}[b][b']
+      tile_gemm<R>(cl, cr, cr, Mb + cr, 2 * cr, 1, false, Rn, chi, 1, false, N1, cr, false, sA, sB);
+      // Le'[b'][b] = sum_{(a,s)} conj(B[(a,s)][b']) M[(a,s)][b]
+      tile_gemm<R>(cr, cr, 2 * cl, Bk, 1, cr, true, Mb, cr, 1, false, Ln, chi, false, sA, sB);
+      // <n_k> |psi|^2 = sum_{a,b} conj(B[a][1][b]) N1[a][b]
+      double re = 0.0;
+      for (int idx = threadIdx.x; idx < cl * cr; idx += blockDim.x) {
+        const int aa = idx / cr, bb = idx - aa * cr;
+        const Tc p = Bk[aa * 2 * cr + cr + bb], q = N1[aa * cr + bb];
+        re += (double)p.x * q.x + (double)p.y * q.y;
+      }
+      re = block_sum_double(re, red);
+      if (threadIdx.x == 0) {
+        const double nk = re / nrm2;
+        a.density[(long long)traj * L + k] = nk;
+        if (kRates) {
+          double* rt = a.rates + (long long)traj * 3 * L + 3 * k;
+          rt[0] = a.gl[k] * nk;
+          rt[1] = a.gg[k] * (1.0 - nk);
+          rt[2] = a.gd[k] * nk;
+        }
+      }
+      __syncthreads();
+      Tc* tmp = Le;
+      Le = Ln;
+      Ln = tmp;
+    }
+    if (kRates && a.decide && threadIdx.x == 0) decide_channel(a, traj);
     __syncthreads();
   }
 }
@@ -1246,8 +1424,8 @@ cudaError_t launch_env(lt_ctx_s* c, int decide, long long step, const int* repla
   a.decide = decide;
   a.step = step;
   a.replay = replay;
-  if (c->prec == LT_MIXED) env_kernel<float><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
-  else env_kernel<double><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
+  if (c->prec == LT_MIXED) env_tiled_kernel<float><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
+  else env_tiled_kernel<double><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1415,8 +1593,8 @@ extern "C" lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, in
   a.scratch_stride = (long long)stride;
   a.density = density;
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == LT_MIXED) env_kernel<float, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
-  else env_kernel<double, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
+  if (precision == LT_MIXED) env_tiled_kernel<float, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
+  else env_tiled_kernel<double, false><<<(int)grid, LT_BLOCK, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? LT_OK : LT_ERR_CUDA;
 }
 
@@ -1425,8 +1603,8 @@ extern "C" lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, in
 int env_grid(lt_ctx_s* c) {
   int occ = 0;
   cudaError_t e = c->prec == LT_MIXED
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_kernel<float>, LT_BLOCK, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_kernel<double>, LT_BLOCK, 0);
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_tiled_kernel<float>, LT_BLOCK, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_tiled_kernel<double>, LT_BLOCK, 0);
   if (e != cudaSuccess || occ < 1) occ = 2;
   if (occ > 8) occ = 8;
   const long long g = (long long)occ * c->num_sms;
