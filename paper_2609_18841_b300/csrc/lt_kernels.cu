@@ -500,6 +500,284 @@ template <typename R> struct BondShape;
 template <> struct BondShape<float> { static constexpr int NT = 256, EPP = 8; };
 template <> struct BondShape<double> { static constexpr int NT = 256, EPP = 4; };
 
+// ---- two-level Householder preconditioning of the row Jacobi ---------------------------
+// The one-sided Jacobi on the rows of X converges slowly when the rows are
+// strongly graded (theta's rows carry the weights Lambda_{b-1}).  With an LQ
+// factorisation X = L1 Q1^+ (Householder reflectors from the rows) followed by a
+// QR factorisation L1 = Q2 R2, the rows of R2 = Q2^+ X Q1 are nearly orthogonal
+// and the sweeps converge in a few rounds (the two-sided preconditioning of
+// Drmac and Veselic, without pivoting).  Q2 is not needed: if the Jacobi turns
+// the rows of R2 into sigma_j w_j^+, the right singular vectors of X are
+// v_j^+ = w_j^+ Q1^+ = w_j^+ H_{r-1} ... H_0.
+// On entry X (planar, m x n, row stride ldp) holds the matrix; on exit
+// X[0:r, 0:r] holds R2 (upper triangular), every other entry is zero, and Vst
+// holds the reflectors of Q1 = H_0 ... H_{r-1}: for a row x, x H_j = x - beta_j
+// (sum_c x_c conj(e_c)) e with e the stored vector of H_j (the tail of row j
+// plus ph alpha in its first entry), acting on columns j..n-1 and packed at
+// offset sum_{i<j} (n - i).
+template <typename R>
+__device__ __forceinline__ void warp_sum2(R& a, R& b) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(FULL, a, o);
+    b += __shfl_xor_sync(FULL, b, o);
+  }
+}
+
+#define LT_QR_CH 8  // entries staged in registers per chunk of a Householder update
+
+template <typename R> struct TinyNorm;
+template <> struct TinyNorm<float> { static constexpr float v = 1e-18f; };
+template <> struct TinyNorm<double> { static constexpr double v = 1e-150; };
+
+// Reflector from the n-j entries x_t = X[p(t)] (stride st from base b0):
+// alpha = |x|, ph = x_0/|x_0|; e = x + ph alpha e_0 is stored at dst, the entries
+// are replaced by (-ph alpha, 0, ...), and beta = 2/|e|^2 is returned (0 when
+// alpha is below TinyNorm, in which case the entries are simply set to zero:
+// they are below any precision of the result).  One warp.
+template <typename R>
+__device__ __forceinline__ R make_reflector(R* Xr, R* Xi, int base, int st, int len,
+                                            typename CT<R>::T* dst) {
+  typedef typename CT<R>::T Tc;
+  const int lane = threadIdx.x & 31;
+  R a2 = 0, dummy = 0;
+  for (int t = lane; t < len; t += 32) {
+    const R u = Xr[base + t * st], w = Xi[base + t * st];
+    a2 = fma(u, u, fma(w, w, a2));
+  }
+  warp_sum2(a2, dummy);
+  const R x0r = Xr[base], x0i = Xi[base];
+  const R alpha = sqrt(a2), ax0 = sqrt(x0r * x0r + x0i * x0i);
+  const bool tiny = !(alpha > TinyNorm<R>::v);
+  const R phr = ax0 > (R)0 ? x0r / ax0 : (R)1, phi = ax0 > (R)0 ? x0i / ax0 : (R)0;
+  for (int t = lane; t < len; t += 32) {
+    Tc e = cmk<Tc>(Xr[base + t * st], Xi[base + t * st]);
+    if (t == 0) {
+      e.x += phr * alpha;
+      e.y += phi * alpha;
+    }
+    dst[t] = tiny ? czero<Tc>() : e;
+    Xr[base + t * st] = (t == 0 && !tiny) ? -phr * alpha : (R)0;
+    Xi[base + t * st] = (t == 0 && !tiny) ? -phi * alpha : (R)0;
+  }
+  return tiny ? (R)0 : (R)2 / (2 * alpha * (alpha + ax0));
+}
+
+template <typename R>
+__device__ void qr_precondition(R* Xr, R* Xi, int ldp, int m, int n, int r,
+                                typename CT<R>::T* Vst, R* beta, typename CT<R>::T* su) {
+  typedef typename CT<R>::T Tc;
+  const int warp = threadIdx.x >> 5;
+  __syncthreads();
+  // LQ: H_j from the tail of row j, applied from the right to the rows below;
+  // each thread owns one row (no reductions across threads)
+  int off = 0;
+  for (int j = 0; j < r; ++j) {
+    Tc* e = Vst + off;
+    const int len = n - j;
+    if (warp == 0) {
+      const R bt = make_reflector<R>(Xr, Xi, j * ldp + j, 1, len, e);
+      if ((threadIdx.x & 31) == 0) beta[j] = bt;
+    }
+    __syncthreads();
+    const R bt = beta[j];
+    if (bt != (R)0) {
+      const Tc* __restrict__ ev = e;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        R* __restrict__ xr = Xr + i * ldp + j;
+        R* __restrict__ xi = Xi + i * ldp + j;
+        R dr = 0, di = 0;  // d = sum_c x_c conj(e_c), in chunks staged in registers
+        for (int c0 = 0; c0 < len; c0 += LT_QR_CH) {
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const bool in = c0 + u < len;
+            a[u] = in ? xr[c0 + u] : (R)0;
+            b[u] = in ? xi[c0 + u] : (R)0;
+            w[u] = in ? ev[c0 + u] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            dr = fma(a[u], w[u].x, fma(b[u], w[u].y, dr));
+            di = fma(b[u], w[u].x, fma(-a[u], w[u].y, di));
+          }
+        }
+        dr *= bt;
+        di *= bt;
+        for (int c0 = 0; c0 < len; c0 += LT_QR_CH) {  // x -= beta d e
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const bool in = c0 + u < len;
+            a[u] = in ? xr[c0 + u] : (R)0;
+            b[u] = in ? xi[c0 + u] : (R)0;
+            w[u] = in ? ev[c0 + u] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            if (c0 + u < len) {
+              xr[c0 + u] = a[u] - fma(dr, w[u].x, -di * w[u].y);
+              xi[c0 + u] = b[u] - fma(dr, w[u].y, di * w[u].x);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    off += len;
+  }
+  // QR of the lower-trapezoidal L1 (columns 0..r-1): reflectors from the columns,
+  // applied from the left to the columns on their right, one thread per column;
+  // Q2 is discarded
+  for (int j = 0; j < r; ++j) {
+    const int len = m - j;
+    if (warp == 0) {
+      const R bt = make_reflector<R>(Xr, Xi, j * ldp + j, ldp, len, su);
+      if ((threadIdx.x & 31) == 0) beta[LT_MAX_DIM] = bt;
+    }
+    __syncthreads();
+    const R bt = beta[LT_MAX_DIM];
+    if (bt != (R)0) {
+      const Tc* __restrict__ uv = su;
+      for (int c = j + 1 + threadIdx.x; c < r; c += blockDim.x) {
+        R* __restrict__ xr = Xr + j * ldp + c;
+        R* __restrict__ xi = Xi + j * ldp + c;
+        R dr = 0, di = 0;  // d = sum_i conj(u_i) x_i
+        for (int t0 = 0; t0 < len; t0 += LT_QR_CH) {
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const bool in = t0 + u < len;
+            a[u] = in ? xr[(t0 + u) * ldp] : (R)0;
+            b[u] = in ? xi[(t0 + u) * ldp] : (R)0;
+            w[u] = in ? uv[t0 + u] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            dr = fma(w[u].x, a[u], fma(w[u].y, b[u], dr));
+            di = fma(w[u].x, b[u], fma(-w[u].y, a[u], di));
+          }
+        }
+        dr *= bt;
+        di *= bt;
+        for (int t0 = 0; t0 < len; t0 += LT_QR_CH) {  // x -= u d
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const bool in = t0 + u < len;
+            a[u] = in ? xr[(t0 + u) * ldp] : (R)0;
+            b[u] = in ? xi[(t0 + u) * ldp] : (R)0;
+            w[u] = in ? uv[t0 + u] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            if (t0 + u < len) {
+              xr[(t0 + u) * ldp] = a[u] - fma(w[u].x, dr, -w[u].y * di);
+              xi[(t0 + u) * ldp] = b[u] - fma(w[u].x, di, w[u].y * dr);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Right singular vectors from the Jacobi rows: for j < k, row p = perm[j] holds
+// sigma_j w_j^+ in its first r entries; scaled to w_j^+ and multiplied by
+// Q1^+ = H_{r-1} ... H_0 it becomes v_j^+ (n entries), written to Y[j].  Four
+// lanes per row, each taking every fourth entry.
+template <typename R>
+__device__ void apply_q1(R* Xr, R* Xi, int ldp, int n, int r, int k, const int* perm,
+                         const double* sig, const typename CT<R>::T* Vst, const R* beta,
+                         typename CT<R>::T* Y, int ldy) {
+  typedef typename CT<R>::T Tc;
+  __syncthreads();
+  const int q = threadIdx.x & 3;
+  const int rows_per_pass = blockDim.x >> 2;
+  const int passes = (k + rows_per_pass - 1) / rows_per_pass;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int j = pass * rows_per_pass + (threadIdx.x >> 2);
+    const bool act = j < k;
+    const int p = act ? perm[j] : 0;
+    R* xr = Xr + p * ldp;
+    R* xi = Xi + p * ldp;
+    if (act) {
+      const double sg = sig[p];
+      const R inv = sg > 0.0 ? (R)(1.0 / sqrt(sg)) : (R)0;
+      for (int c = q; c < n; c += 4) {
+        xr[c] *= inv;
+        xi[c] *= inv;
+      }
+    }
+    int off = r * n - r * (r - 1) / 2;
+    for (int l = r - 1; l >= 0; --l) {
+      off -= n - l;
+      const R bt = beta[l];
+      if (bt == (R)0) continue;  // uniform across the block
+      const Tc* e = Vst + off;
+      const int len = n - l;
+      const Tc* __restrict__ ev = e;
+      R dr = 0, di = 0;  // d = sum_c x_c conj(e_c)
+      if (act)
+        for (int c0 = q; c0 < len; c0 += 4 * LT_QR_CH) {
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const int c = c0 + 4 * u;
+            const bool in = c < len;
+            a[u] = in ? xr[l + c] : (R)0;
+            b[u] = in ? xi[l + c] : (R)0;
+            w[u] = in ? ev[c] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            dr = fma(a[u], w[u].x, fma(b[u], w[u].y, dr));
+            di = fma(b[u], w[u].x, fma(-a[u], w[u].y, di));
+          }
+        }
+      dr += __shfl_xor_sync(FULL, dr, 1);
+      di += __shfl_xor_sync(FULL, di, 1);
+      dr += __shfl_xor_sync(FULL, dr, 2);
+      di += __shfl_xor_sync(FULL, di, 2);
+      dr *= bt;
+      di *= bt;
+      if (act)
+        for (int c0 = q; c0 < len; c0 += 4 * LT_QR_CH) {  // x -= beta d e
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const int c = c0 + 4 * u;
+            const bool in = c < len;
+            a[u] = in ? xr[l + c] : (R)0;
+            b[u] = in ? xi[l + c] : (R)0;
+            w[u] = in ? ev[c] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const int c = c0 + 4 * u;
+            if (c < len) {
+              xr[l + c] = a[u] - fma(dr, w[u].x, -di * w[u].y);
+              xi[l + c] = b[u] - fma(dr, w[u].y, di * w[u].x);
+            }
+          }
+        }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * n; idx += blockDim.x) {
+    const int j = idx / n, c = idx - j * n;
+    const int p = perm[j];
+    Y[j * ldy + c] = cmk<Tc>(Xr[p * ldp + c], Xi[p * ldp + c]);
+  }
+}
+
 // ---- the two-site update and the one-site canonical-form steps -----------------------------
 // mode 0: two-site update with the layer's gate (Eq. Theta): theta = Lambda_{b-1}
 //         G (B_b B_{b+1}), SVD, keep k, Lambda_b = S_k/|S_k|, B_{b+1} = V_k^+,
@@ -532,6 +810,8 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
   __shared__ double s_lamL[LT_MAX_CHI];
   __shared__ int s_k, s_nrot;
   __shared__ double s_norm, s_wdisc;
+  __shared__ R s_beta[LT_MAX_DIM + 1];
+  __shared__ Tc s_u[LT_MAX_DIM];
 
   R* W = a.use_smem ? reinterpret_cast<R*>(smem_raw)
                     : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
@@ -596,25 +876,32 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
         Xi[r * ldp + c] = v.y;
       }
     }
+    // two-level Householder preconditioning; the Jacobi then acts on the r x r
+    // upper-triangular factor (its layout fits inside the one chosen for mJ x nJ)
+    const int rr = mJ < nJ ? mJ : nJ;
+    qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
+    bool blk2;
+    int npad2, mp2;
+    jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
     int sweeps;
-    if (blocked) {
-      if (npad == 64)
+    if (blk2) {
+      if (npad2 == 64)
         sweeps = jacobi_blocked<1>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
-                                   mpJ, nJ, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
+                                   mp2, rr, npad2, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
       else
         sweeps = jacobi_blocked<2>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
-                                   mpJ, nJ, npad, reinterpret_cast<float*>(s_nrm), &s_nrot,
+                                   mp2, rr, npad2, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
     } else {
-      sweeps = jacobi_rows<R, BondShape<R>::EPP>(Xr, Xi, ldp, mpJ, nJ, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+      sweeps = jacobi_rows<R, BondShape<R>::EPP>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
     }
     // singular values squared, accumulated in double
     {
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-      for (int r = warp; r < mJ; r += nw) {
+      for (int r = warp; r < rr; r += nw) {
         double acc = 0.0;
-        for (int c = lane; c < nJ; c += 32) {
+        for (int c = lane; c < rr; c += 32) {
           const double u = Xr[r * ldp + c], v = Xi[r * ldp + c];
           acc += u * u + v * v;
         }
@@ -624,10 +911,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
       }
     }
     __syncthreads();
-    for (int r = tid; r < mJ; r += blockDim.x) {
+    for (int r = tid; r < rr; r += blockDim.x) {
       const double v = s_sig[r];
       int rank = 0;
-      for (int j = 0; j < mJ; ++j) {
+      for (int j = 0; j < rr; ++j) {
         const double u = s_sig[j];
         rank += (u > v) || (u == v && j < r);
       }
@@ -636,7 +923,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     __syncthreads();
     if (tid == 0) {
       double total = 0.0;
-      for (int j = 0; j < mJ; ++j) total += s_sig[j];
+      for (int j = 0; j < rr; ++j) total += s_sig[j];
       const double s0 = s_sig[s_perm[0]];
       int k = 0;
       if (s0 > 0.0) {
@@ -656,9 +943,13 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
         // algorithmic real flops: the Jacobi (row norms each sweep and at the end,
         // one complex inner product per pair per sweep, 24 nJ per applied
         // rotation) plus the contractions of the mode (theta formed once)
-        const double dm_ = mJ, dn_ = nJ;
-        const double pairs = 0.5 * dm_ * (dm_ - 1.0) * sweeps;
-        double fl = 4.0 * dm_ * dn_ * (sweeps + 1) + 8.0 * dn_ * pairs + 24.0 * dn_ * s_nrot;
+        // (the Householder preconditioning: sum_j 16 (mJ-j-1)(nJ-j) for the
+        // LQ, sum_j 16 (mJ-j)(r-j-1) for the QR, 16 k sum_l (nJ-l) to apply Q1)
+        const double dr_ = rr;
+        const double pairs = 0.5 * dr_ * (dr_ - 1.0) * sweeps;
+        double fl = 4.0 * dr_ * dr_ * (sweeps + 1) + 8.0 * dr_ * pairs + 24.0 * dr_ * s_nrot;
+        for (int j = 0; j < rr; ++j)
+          fl += 16.0 * (mJ - j - 1) * (nJ - j) + 16.0 * (mJ - j) * (rr - j - 1) + 16.0 * k * (nJ - j);
         const double mL = 2.0 * chiL, nR = 2.0 * chiR;
         if (mode == 0) fl += 8.0 * mL * nR * (chiM + 4) + 8.0 * mL * k * nR;
         else if (mode == 1) fl += 8.0 * mL * nR * chiM + 8.0 * mL * k * nR;
@@ -673,14 +964,8 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     }
     __syncthreads();
     const int k = s_k;
-    // V_k^+ rows: Y[j] = X[perm j] / sigma_j
-    for (int idx = tid; idx < k * nJ; idx += blockDim.x) {
-      const int j = idx / nJ, c = idx - j * nJ;
-      const int r = s_perm[j];
-      const double sg = s_sig[r];
-      const R inv = sg > 0.0 ? (R)(1.0 / sqrt(sg)) : (R)0;
-      Y[j * ld + c] = cmk<Tc>(Xr[r * ldp + c] * inv, Xi[r * ldp + c] * inv);
-    }
+    // V_k^+ rows: row perm j holds sigma_j w_j^+; v_j^+ = w_j^+ Q1^+ goes to Y[j]
+    apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
     __syncthreads();
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
