@@ -211,8 +211,12 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2609_18841_b300 import lindtebd as lt
+    from paper_2609_18841_b300 import shard
 
     L, chi, n_traj = workloads.W3["L"], workloads.W3["chi_max"], args.traj
+    # weak scaling: each rank owns n_traj trajectories of a world * n_traj ensemble
+    offset, n_loc = shard.shard_range(world * n_traj, rank, world)
+    assert n_loc == n_traj
     dt = workloads.W3["dt"]
     stream = torch.cuda.Stream()
     mps, packed = state_pool(L, chi, POOL)
@@ -224,7 +228,7 @@ def run_ours(args):
 
     # ---- headline: mixed precision ------------------------------------------------------
     ens = lt.Ensemble(L, chi, n_traj, precision=lt.LT_MIXED, init="neel",
-                      traj_offset=rank * n_traj, stream=stream.cuda_stream, **w3_kwargs("mixed"))
+                      traj_offset=offset, stream=stream.cuda_stream, **w3_kwargs("mixed"))
     upload(lt, ens.ctx, packed, n_traj)
     layers = [(0, dt / 2), (1, dt), (0, dt / 2)]
     step = 0
@@ -330,12 +334,14 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         e = lt.Ensemble(L, chi, n_traj, precision=lt.LT_MIXED, init="neel",
-                        traj_offset=rank * n_traj, stream=stream.cuda_stream,
+                        traj_offset=offset, stream=stream.cuda_stream,
                         **w3_kwargs("mixed"))
         h2d = upload(lt, e.ctx, None, n_traj, pinned=pinned)
         for _ in range(args.steps):
             lt.lt_step(e.ctx, 1)
             lt.lt_measure_density(e.ctx, L, n_traj, out=(mean_h, sem_h))
+        # ensemble statistics over all ranks (the one collective of the sharded path)
+        shard.combine_mean_sem(mean_h, sem_h, n_traj, device=torch.device("cuda", local))
         ce = e.counters()
         e.close()
         t1 = time.perf_counter()

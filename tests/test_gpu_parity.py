@@ -219,3 +219,27 @@ def test_large_dt_is_reported_and_poisons_the_context():
         ens.step(1)
     assert e.value.status == lt.LT_ERR_STATE
     ens.close()
+
+
+@pytest.mark.parametrize("precision_name", ["fp64", "mixed"])
+def test_trajectory_shards_reproduce_the_unsharded_ensemble(precision_name):
+    """Ranks own contiguous ranges of global trajectory ids (traj_offset); the
+    jump draws are keyed by the global id, so two shards must give exactly the
+    trajectories of one context holding all of them."""
+    from paper_2609_18841_b300 import shard
+    lt = _lt()
+    prec = lt.LT_FP64 if precision_name == "fp64" else lt.LT_MIXED
+    L, chi, n_total, steps = 10, 8, 9, 8
+    kw = dict(precision=prec, init="neel", dt=0.05, gamma_loss=0.6, seed=5)
+    with lt.Ensemble(L, chi, n_total, **kw) as whole:
+        whole_j = gpu_steps(whole, oracle_cfg(workloads.W1, L=L, chi=chi, dt=0.05), steps)
+        _, _, whole_d = whole.density(per_traj=True)
+    parts_j, parts_d = [], []
+    for r in range(2):
+        off, n = shard.shard_range(n_total, r, 2)
+        with lt.Ensemble(L, chi, n, traj_offset=off, **kw) as e:
+            parts_j.append(gpu_steps(e, oracle_cfg(workloads.W1, L=L, chi=chi, dt=0.05), steps))
+            parts_d.append(e.density(per_traj=True)[2])
+    assert whole_j.max() >= 0, "the case should contain jumps"
+    assert np.array_equal(np.concatenate(parts_j), whole_j)
+    assert np.array_equal(np.concatenate(parts_d), whole_d)
