@@ -687,6 +687,218 @@ __device__ void qr_precondition(R* Xr, R* Xi, int ldp, int m, int n, int r,
   }
 }
 
+// ---- the same preconditioning in single precision, rows held in registers -------------
+// Identical factorisation and reflector convention as qr_precondition, but each
+// row stays in the registers of a lane pair for the whole factorisation: thread
+// t holds row t >> 1, lane q = t & 1 the columns c = 2s + q (s < 64), packed as
+// float2 pairs h = s >> 1 (column 4h + q in .x, 4h + 2 + q in .y).  A step only
+// reads its reflector from shared memory, and the lane pair of the next row
+// builds the next reflector into the other of two buffers, so each reflector
+// costs one barrier.  The QR of L1 runs as the LQ of L1^+ (L1 is written
+// conjugate-transposed to shared memory in between): if L1^+ = L' Q^+ then
+// L1 = Q L'^+, so R2 = L'^+ with the same diagonal phases.
+#define LT_LQ_HALF 66  // floats between the two lanes' halves of a reflector buffer
+
+struct LQRow {
+  float2 r[32], i[32];
+};
+
+__device__ __forceinline__ bool lq_block_live(int hb, int j0, int ncol) {
+  return 16 * hb + 16 > j0 && 16 * hb < ncol;  // columns 16 hb .. 16 hb + 15
+}
+
+__device__ __forceinline__ void lq_load(LQRow& x, const float* Xr, const float* Xi, int ld,
+                                        int row, int nrow, int ncol, int q) {
+#pragma unroll
+  for (int h = 0; h < 32; ++h) {
+    const int c0 = 4 * h + q, c1 = c0 + 2;
+    const bool ok = row < nrow;
+    x.r[h] = make_float2(ok && c0 < ncol ? Xr[row * ld + c0] : 0.f,
+                         ok && c1 < ncol ? Xr[row * ld + c1] : 0.f);
+    x.i[h] = make_float2(ok && c0 < ncol ? Xi[row * ld + c0] : 0.f,
+                         ok && c1 < ncol ? Xi[row * ld + c1] : 0.f);
+  }
+}
+
+// x <- x - beta (sum_c x_c conj(e_c)) e over the live column blocks; er/ei is
+// this lane's half of the reflector buffer
+__device__ __forceinline__ void lq_apply(LQRow& x, const float* er, const float* ei, float bt,
+                                         int j0, int ncol) {
+  float2 A = make_float2(0.f, 0.f), B = A, C = A, D = A;
+#pragma unroll
+  for (int hb = 0; hb < 8; ++hb) {
+    if (lq_block_live(hb, j0, ncol)) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int h = 4 * hb + u;
+        const float2 a = *reinterpret_cast<const float2*>(er + 2 * h);
+        const float2 b = *reinterpret_cast<const float2*>(ei + 2 * h);
+        A = pfma(x.r[h], a, A);
+        B = pfma(x.i[h], b, B);
+        C = pfma(x.i[h], a, C);
+        D = pfma(x.r[h], b, D);
+      }
+    }
+  }
+  float dr = (A.x + A.y) + (B.x + B.y), di = (C.x + C.y) - (D.x + D.y);
+  dr += __shfl_xor_sync(FULL, dr, 1);
+  di += __shfl_xor_sync(FULL, di, 1);
+  const float2 NDR = make_float2(-dr * bt, -dr * bt);
+  const float2 DI = make_float2(di * bt, di * bt), NDI = make_float2(-di * bt, -di * bt);
+#pragma unroll
+  for (int hb = 0; hb < 8; ++hb) {
+    if (lq_block_live(hb, j0, ncol)) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int h = 4 * hb + u;
+        const float2 a = *reinterpret_cast<const float2*>(er + 2 * h);
+        const float2 b = *reinterpret_cast<const float2*>(ei + 2 * h);
+        x.r[h] = pfma(NDR, a, pfma(DI, b, x.r[h]));   // xr - dr ar + di ai
+        x.i[h] = pfma(NDR, b, pfma(NDI, a, x.i[h]));  // xi - dr ai - di ar
+      }
+    }
+  }
+}
+
+// Reflector from row jn (columns jn .. ncol-1), built by that row's lane pair
+// into the buffer ebr/ebi (both halves): e = x + ph alpha e_jn, entries below
+// jn zero; beta = 2 / |e|^2 (0 below TinyNorm) and the diagonal -ph alpha of L.
+__device__ __forceinline__ void lq_build(const LQRow& x, float* ebr, float* ebi, int jn, int ncol,
+                                         int q, float* bt_out, float2* diag) {
+  const unsigned pm = 3u << (threadIdx.x & 30);
+  float* er = ebr + q * LT_LQ_HALF;
+  float* ei = ebi + q * LT_LQ_HALF;
+  float a2 = 0.f;
+#pragma unroll
+  for (int hb = 0; hb < 8; ++hb) {
+    if (lq_block_live(hb, jn, ncol)) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int h = 4 * hb + u, c0 = 4 * h + q;
+        float2 vr = x.r[h], vi = x.i[h];
+        if (c0 < jn) {
+          vr.x = 0.f;
+          vi.x = 0.f;
+        }
+        if (c0 + 2 < jn) {
+          vr.y = 0.f;
+          vi.y = 0.f;
+        }
+        a2 = fmaf(vr.x, vr.x, fmaf(vi.x, vi.x, a2));
+        a2 = fmaf(vr.y, vr.y, fmaf(vi.y, vi.y, a2));
+        *reinterpret_cast<float2*>(er + 2 * h) = vr;
+        *reinterpret_cast<float2*>(ei + 2 * h) = vi;
+      }
+    }
+  }
+  a2 += __shfl_xor_sync(pm, a2, 1);
+  __syncwarp(pm);
+  if (q == 0) {
+    const int p = (jn & 1) * LT_LQ_HALF + (jn >> 1);
+    const float x0r = ebr[p], x0i = ebi[p];
+    const float alpha = sqrtf(a2), ax0 = sqrtf(x0r * x0r + x0i * x0i);
+    const bool tiny = !(alpha > TinyNorm<float>::v);
+    const float phr = ax0 > 0.f ? x0r / ax0 : 1.f, phi = ax0 > 0.f ? x0i / ax0 : 0.f;
+    ebr[p] = x0r + phr * alpha;
+    ebi[p] = x0i + phi * alpha;
+    *bt_out = tiny ? 0.f : 2.f / (2.f * alpha * (alpha + ax0));
+    diag[jn] = tiny ? make_float2(0.f, 0.f) : make_float2(-phr * alpha, -phi * alpha);
+  }
+  __syncwarp(pm);
+}
+
+// LQ of the nrow x ncol (<= 128 x 128) matrix in the LQRow of every thread
+// (rows >= nrow zero), r reflectors.  On return row i of L is x for columns
+// below i, diag[i] at column i and zero beyond.  With Vst, reflector j is also
+// stored packed there (ncol - j entries from column j), its beta in beta[j].
+__device__ void lq_rows(LQRow& x, int nrow, int ncol, int r, float2* Vst, float* beta,
+                        float (*ebr)[2 * LT_LQ_HALF], float (*ebi)[2 * LT_LQ_HALF], float* bt2,
+                        float2* diag) {
+  const int t = threadIdx.x, row = t >> 1, q = t & 1;
+  const int wrow0 = (t >> 5) * 16;
+  if (row == 0) lq_build(x, ebr[0], ebi[0], 0, ncol, q, bt2, diag);
+  __syncthreads();
+  int off = 0;
+  for (int j = 0; j < r; ++j) {
+    const int b = j & 1;
+    if (Vst) {
+      for (int c = j + t; c < ncol; c += blockDim.x) {
+        const int p = (c & 1) * LT_LQ_HALF + (c >> 1);
+        Vst[off + c - j] = make_float2(ebr[b][p], ebi[b][p]);
+      }
+      if (t == 0) beta[j] = bt2[b];
+      off += ncol - j;
+    }
+    const float bt = bt2[b];
+    // rows <= j are finished (H_j only touches their columns >= j, which the
+    // caller replaces by the diagonal and zeros), so warps holding only such
+    // rows skip the step
+    if (bt != 0.f && wrow0 + 15 > j && wrow0 < nrow)
+      lq_apply(x, ebr[b] + q * LT_LQ_HALF, ebi[b] + q * LT_LQ_HALF, bt, j, ncol);
+    if (j + 1 < r && row == j + 1) lq_build(x, ebr[b ^ 1], ebi[b ^ 1], j + 1, ncol, q, bt2 + (b ^ 1), diag);
+    __syncthreads();
+  }
+}
+
+// Row `row` of L from the LQRow (see lq_rows), entry of column c, conjugated
+__device__ __forceinline__ float2 lq_entry_conj(const LQRow& x, int h, int u, int q, int row,
+                                                int nrow, const float2* diag) {
+  const int c = 4 * h + 2 * u + q;
+  float2 v = make_float2(0.f, 0.f);
+  if (row < nrow) {
+    if (c < row) v = make_float2(u ? x.r[h].y : x.r[h].x, u ? x.i[h].y : x.i[h].x);
+    else if (c == row) v = diag[row];
+  }
+  return make_float2(v.x, -v.y);
+}
+
+// Single-precision qr_precondition (same contract, blockDim.x = 256, m, n <= 128;
+// X[0:mp2, 0:npad2] is the window the Jacobi reads afterwards)
+__device__ void qr_precondition_reg(float* Xr, float* Xi, int ldp, int m, int n, int r,
+                                    int mp2, int npad2, float2* Vst, float* beta) {
+  __shared__ __align__(16) float s_ebr[2][2 * LT_LQ_HALF];
+  __shared__ __align__(16) float s_ebi[2][2 * LT_LQ_HALF];
+  __shared__ float s_bt2[2];
+  __shared__ float2 s_diag[LT_MAX_DIM];
+  const int t = threadIdx.x, row = t >> 1, q = t & 1;
+  LQRow x;
+  __syncthreads();
+  lq_load(x, Xr, Xi, ldp, row, m, n, q);
+  // level 1: X = L1 Q1^+ (r reflectors kept for the right singular vectors)
+  lq_rows(x, m, n, r, Vst, beta, s_ebr, s_ebi, s_bt2, s_diag);
+  // L1^+ (r x m) into X with row stride m: r m <= mcap ldp, and X is no longer read
+#pragma unroll
+  for (int h = 0; h < 32; ++h)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int c = 4 * h + 2 * u + q;
+      if (row < m && c < r) {
+        const float2 v = lq_entry_conj(x, h, u, q, row, m, s_diag);
+        Xr[c * m + row] = v.x;
+        Xi[c * m + row] = v.y;
+      }
+    }
+  __syncthreads();
+  lq_load(x, Xr, Xi, m, row, r, m, q);
+  // level 2: L1^+ = L' Q^+ (the reflectors are not needed)
+  lq_rows(x, r, m, r, nullptr, nullptr, s_ebr, s_ebi, s_bt2, s_diag);
+  // R2 = L'^+ into the Jacobi window (zero outside r x r)
+  if (row < npad2) {
+#pragma unroll
+    for (int h = 0; h < 32; ++h)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int a = 4 * h + 2 * u + q;
+        if (a < mp2) {
+          const float2 v = lq_entry_conj(x, h, u, q, row, r, s_diag);
+          Xr[a * ldp + row] = v.x;
+          Xi[a * ldp + row] = v.y;
+        }
+      }
+  }
+  __syncthreads();
+}
+
 // Right singular vectors from the Jacobi rows: for j < k, row p = perm[j] holds
 // sigma_j w_j^+ in its first r entries; scaled to w_j^+ and multiplied by
 // Q1^+ = H_{r-1} ... H_0 it becomes v_j^+ (n entries), written to Y[j].  Four
@@ -778,6 +990,96 @@ __device__ void apply_q1(R* Xr, R* Xi, int ldp, int n, int r, int k, const int* 
   }
 }
 
+// Single-precision apply_q1 (same contract; columns >= r of the Jacobi rows are
+// taken as zero): four lanes per row, lane q holding columns 4s + q (s < 32) as
+// float2 pairs (8h + q, 8h + 4 + q); the reflectors are read from their packed
+// store with no barrier between them, and Y (which overlays that store) is
+// written after one barrier at the end.
+__device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, int r, int k,
+                             const int* perm, const double* sig, const float2* Vst,
+                             const float* beta, float2* Y, int ldy) {
+  __syncthreads();
+  const int q = threadIdx.x & 3, j = threadIdx.x >> 2;
+  const bool act = j < k;
+  float2 xr[16], xi[16];
+#pragma unroll
+  for (int h = 0; h < 16; ++h) {
+    xr[h] = make_float2(0.f, 0.f);
+    xi[h] = xr[h];
+  }
+  if ((threadIdx.x >> 5) * 8 < k) {  // warp-uniform: the warp holds a live row
+    const int p = act ? perm[j] : 0;
+    const float inv = act && sig[p] > 0.0 ? (float)(1.0 / sqrt(sig[p])) : 0.f;
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+      const int c0 = 8 * h + q, c1 = c0 + 4;
+      if (act && c0 < r) {
+        xr[h].x = Xr[p * ldp + c0] * inv;
+        xi[h].x = Xi[p * ldp + c0] * inv;
+      }
+      if (act && c1 < r) {
+        xr[h].y = Xr[p * ldp + c1] * inv;
+        xi[h].y = Xi[p * ldp + c1] * inv;
+      }
+    }
+    int off = r * n - r * (r - 1) / 2;
+    for (int l = r - 1; l >= 0; --l) {
+      off -= n - l;
+      const float bt = beta[l];
+      if (bt == 0.f) continue;  // uniform across the block
+      const float2* e = Vst + off - l;  // e[c], l <= c < n
+      float dr0 = 0.f, di0 = 0.f, dr1 = 0.f, di1 = 0.f;
+#pragma unroll
+      for (int sb = 0; sb < 8; ++sb) {
+        if (16 * sb + 16 > l && 16 * sb < n) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int h = 2 * sb + u, c0 = 8 * h + q, c1 = c0 + 4;
+            const float2 e0 = (c0 >= l && c0 < n) ? e[c0] : make_float2(0.f, 0.f);
+            const float2 e1 = (c1 >= l && c1 < n) ? e[c1] : make_float2(0.f, 0.f);
+            dr0 = fmaf(xr[h].x, e0.x, fmaf(xi[h].x, e0.y, dr0));
+            di0 = fmaf(xi[h].x, e0.x, fmaf(-xr[h].x, e0.y, di0));
+            dr1 = fmaf(xr[h].y, e1.x, fmaf(xi[h].y, e1.y, dr1));
+            di1 = fmaf(xi[h].y, e1.x, fmaf(-xr[h].y, e1.y, di1));
+          }
+        }
+      }
+      float dr = dr0 + dr1, di = di0 + di1;
+      dr += __shfl_xor_sync(FULL, dr, 1);
+      di += __shfl_xor_sync(FULL, di, 1);
+      dr += __shfl_xor_sync(FULL, dr, 2);
+      di += __shfl_xor_sync(FULL, di, 2);
+      dr *= bt;
+      di *= bt;
+#pragma unroll
+      for (int sb = 0; sb < 8; ++sb) {
+        if (16 * sb + 16 > l && 16 * sb < n) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int h = 2 * sb + u, c0 = 8 * h + q, c1 = c0 + 4;
+            const float2 e0 = (c0 >= l && c0 < n) ? e[c0] : make_float2(0.f, 0.f);
+            const float2 e1 = (c1 >= l && c1 < n) ? e[c1] : make_float2(0.f, 0.f);
+            xr[h].x -= fmaf(dr, e0.x, -di * e0.y);
+            xi[h].x -= fmaf(dr, e0.y, di * e0.x);
+            xr[h].y -= fmaf(dr, e1.x, -di * e1.y);
+            xi[h].y -= fmaf(dr, e1.y, di * e1.x);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();  // every reflector read before Y overwrites their store
+  if (act) {
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+      const int c0 = 8 * h + q, c1 = c0 + 4;
+      if (c0 < n) Y[j * ldy + c0] = make_float2(xr[h].x, xi[h].x);
+      if (c1 < n) Y[j * ldy + c1] = make_float2(xr[h].y, xi[h].y);
+    }
+  }
+}
+
+
 // ---- the two-site update and the one-site canonical-form steps -----------------------------
 // mode 0: two-site update with the layer's gate (Eq. Theta): theta = Lambda_{b-1}
 //         G (B_b B_{b+1}), SVD, keep k, Lambda_b = S_k/|S_k|, B_{b+1} = V_k^+,
@@ -791,6 +1093,14 @@ __device__ void apply_q1(R* Xr, R* Xi, int ldp, int n, int r, int k, const int* 
 // the Jacobi matrix planar (2 mcap ldp reals; in mode 0/1 later theta~), then
 // V_k^+ rows (k x (nJ+1) complex); in mode 0 the region after theta first
 // stages B_{b+1}, in mode 2 the region after V_k^+ stages the new site tensors.
+// sum_{j<r} (a - j)(b - j), or sum_{j<r} (a - j) when `linear`
+__device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear = false) {
+  const long long R = r, A = a, B = b;
+  const long long s1 = R * (R - 1) / 2, s2 = (R - 1) * R * (2 * R - 1) / 6;
+  if (linear) return R * A - s1;
+  return R * A * B - (A + B) * s1 + s2;
+}
+
 template <typename R>
 __device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
   blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64;
@@ -879,10 +1189,14 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     // two-level Householder preconditioning; the Jacobi then acts on the r x r
     // upper-triangular factor (its layout fits inside the one chosen for mJ x nJ)
     const int rr = mJ < nJ ? mJ : nJ;
-    qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
     bool blk2;
     int npad2, mp2;
     jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
+    if constexpr (sizeof(R) == 4)
+      qr_precondition_reg(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ,
+                          rr, mp2, npad2, reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta));
+    else
+      qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
     int sweeps;
     if (blk2) {
       if (npad2 == 64)
@@ -911,61 +1225,80 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
       }
     }
     __syncthreads();
+    // descending order; non-negative doubles order like their bit patterns,
+    // which keeps the comparisons off the double-precision pipe
     for (int r = tid; r < rr; r += blockDim.x) {
-      const double v = s_sig[r];
+      const long long v = __double_as_longlong(s_sig[r]);
       int rank = 0;
       for (int j = 0; j < rr; ++j) {
-        const double u = s_sig[j];
+        const long long u = __double_as_longlong(s_sig[j]);
         rank += (u > v) || (u == v && j < r);
       }
       s_perm[rank] = r;
     }
     __syncthreads();
-    if (tid == 0) {
-      double total = 0.0;
-      for (int j = 0; j < rr; ++j) total += s_sig[j];
+    if (tid < 32) {
+      // k = #{sigma_j > cut sigma_0} (capped at kmax, at least 1), compared
+      // as sigma_j^2 > cut^2 sigma_0^2; kept and total weights by warp sums
+      const int lane = tid;
       const double s0 = s_sig[s_perm[0]];
-      int k = 0;
-      if (s0 > 0.0) {
-        const double thr = a.cut * sqrt(s0);
-        while (k < kmax && sqrt(s_sig[s_perm[k]]) > thr) ++k;
-      } else {
-        atomicOr(a.err, LT_EBIT_THETA_ZERO);
+      const double thr2 = a.cut * a.cut * s0;
+      double total = 0.0;
+      int cnt = 0;
+      for (int j = lane; j < rr; j += 32) {
+        total += s_sig[j];
+        cnt += (j < kmax && s_sig[s_perm[j]] > thr2) ? 1 : 0;
       }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        total += __shfl_xor_sync(FULL, total, o);
+        cnt += __shfl_xor_sync(FULL, cnt, o);
+      }
+      int k = s0 > 0.0 ? cnt : 0;
       if (k < 1) k = 1;
       double kept = 0.0;
-      for (int j = 0; j < k; ++j) kept += s_sig[s_perm[j]];
-      s_k = k;
-      s_norm = kept > 0.0 ? sqrt(kept) : 1.0;
-      s_wdisc = total > 0.0 ? (total - kept) / total : 0.0;
-      if (a.sweep_hist) atomicAdd(a.sweep_hist + (sweeps < 63 ? sweeps : 63), 1);
-      if (a.counters) {
-        // algorithmic real flops: the Jacobi (row norms each sweep and at the end,
-        // one complex inner product per pair per sweep, 24 nJ per applied
-        // rotation) plus the contractions of the mode (theta formed once)
-        // (the Householder preconditioning: sum_j 16 (mJ-j-1)(nJ-j) for the
-        // LQ, sum_j 16 (mJ-j)(r-j-1) for the QR, 16 k sum_l (nJ-l) to apply Q1)
-        const double dr_ = rr;
-        const double pairs = 0.5 * dr_ * (dr_ - 1.0) * sweeps;
-        double fl = 4.0 * dr_ * dr_ * (sweeps + 1) + 8.0 * dr_ * pairs + 24.0 * dr_ * s_nrot;
-        for (int j = 0; j < rr; ++j)
-          fl += 16.0 * (mJ - j - 1) * (nJ - j) + 16.0 * (mJ - j) * (rr - j - 1) + 16.0 * k * (nJ - j);
-        const double mL = 2.0 * chiL, nR = 2.0 * chiR;
-        if (mode == 0) fl += 8.0 * mL * nR * (chiM + 4) + 8.0 * mL * k * nR;
-        else if (mode == 1) fl += 8.0 * mL * nR * chiM + 8.0 * mL * k * nR;
-        else fl += 8.0 * mL * chiM * k + 8.0 * k * chiM * nR;
-        atomicAdd(a.counters + 0, 1ull);
-        atomicAdd(a.counters + 1, (unsigned long long)s_nrot);
-        atomicAdd(a.counters + 2, (unsigned long long)pairs);
-        atomicAdd(a.counters + (a.gates ? 3 : 4), (unsigned long long)fl);
-        if (a.gates) atomicAdd(a.counters + 5, 1ull);
+      for (int j = lane; j < k; j += 32) kept += s_sig[s_perm[j]];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+      if (lane == 0) {
+        if (!(s0 > 0.0)) atomicOr(a.err, LT_EBIT_THETA_ZERO);
+        s_k = k;
+        s_norm = kept > 0.0 ? sqrt(kept) : 1.0;
+        s_wdisc = total > 0.0 ? (total - kept) / total : 0.0;
+        if (a.sweep_hist) atomicAdd(a.sweep_hist + (sweeps < 63 ? sweeps : 63), 1);
+        if (a.counters) {
+          // algorithmic real flops: the Jacobi (row norms each sweep and at the end,
+          // one complex inner product per pair per sweep, 24 nJ per applied
+          // rotation), the Householder preconditioning (sum_j 16 (mJ-j-1)(nJ-j)
+          // for the LQ, sum_j 16 (mJ-j)(r-j-1) for the QR, 16 k sum_l (nJ-l) to
+          // apply Q1) and the contractions of the mode (theta formed once)
+          const double dr_ = rr;
+          const double pairs = 0.5 * dr_ * (dr_ - 1.0) * sweeps;
+          double fl = 4.0 * dr_ * dr_ * (sweeps + 1) + 8.0 * dr_ * pairs + 24.0 * dr_ * s_nrot;
+          fl += 16.0 * (double)(sum_prod(mJ - 1, nJ, rr) + sum_prod(mJ, rr - 1, rr) +
+                                (long long)k * sum_prod(nJ, 1, rr, true));
+          const double mL = 2.0 * chiL, nR = 2.0 * chiR;
+          if (mode == 0) fl += 8.0 * mL * nR * (chiM + 4) + 8.0 * mL * k * nR;
+          else if (mode == 1) fl += 8.0 * mL * nR * chiM + 8.0 * mL * k * nR;
+          else fl += 8.0 * mL * chiM * k + 8.0 * k * chiM * nR;
+          atomicAdd(a.counters + 0, 1ull);
+          atomicAdd(a.counters + 1, (unsigned long long)s_nrot);
+          atomicAdd(a.counters + 2, (unsigned long long)pairs);
+          atomicAdd(a.counters + (a.gates ? 3 : 4), (unsigned long long)fl);
+          if (a.gates) atomicAdd(a.counters + 5, 1ull);
+        }
+        if (sweeps > a.max_sweeps) atomicOr(a.err, LT_EBIT_NOCONV);
       }
-      if (sweeps > a.max_sweeps) atomicOr(a.err, LT_EBIT_NOCONV);
     }
     __syncthreads();
     const int k = s_k;
     // V_k^+ rows: row perm j holds sigma_j w_j^+; v_j^+ = w_j^+ Q1^+ goes to Y[j]
-    apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
+    if constexpr (sizeof(R) == 4)
+      apply_q1_reg(reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi), ldp, nJ,
+                   rr, k, s_perm, s_sig, reinterpret_cast<const float2*>(Y),
+                   reinterpret_cast<const float*>(s_beta), reinterpret_cast<float2*>(Y), ld);
+    else
+      apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
     __syncthreads();
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
@@ -1895,3 +2228,4 @@ int env_grid(lt_ctx_s* c) {
   const long long g = (long long)occ * c->num_sms;
   return (int)(g < c->n_traj ? g : c->n_traj);
 }
+
