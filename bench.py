@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--traj", type=int, default=workloads.W3["n_traj"])
     ap.add_argument("--fp64-traj", type=int, default=128)
+    ap.add_argument("--acc-traj", type=int, default=32)
+    ap.add_argument("--acc-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -323,6 +325,38 @@ def run_ours(args):
                 "n_traj": n64, "steps": 1}
         e64.close()
 
+    # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
+    accuracy = None
+    if args.acc_traj > 0 and rank == 0:
+        na = args.acc_traj
+        ea = lt.Ensemble(L, chi, na, precision=lt.LT_FP64, init="neel",
+                         stream=stream.cuda_stream, **w3_kwargs("fp64"))
+        em = lt.Ensemble(L, chi, na, precision=lt.LT_MIXED, init="neel",
+                         stream=stream.cuda_stream, **w3_kwargs("mixed"))
+        upload(lt, ea.ctx, packed, na)
+        upload(lt, em.ctx, packed, na)
+        jumps = 0
+        for s in range(args.acc_steps):
+            ch = np.ascontiguousarray(ea.apply_jumps(s), np.int32)
+            em.apply_jumps(s, ch)
+            jumps += int((ch >= 0).sum())
+            for parity, tau in layers:
+                ea.apply_layer(parity, tau)
+                em.apply_layer(parity, tau)
+        _, _, d64 = ea.density(per_traj=True)
+        _, _, dmx = em.density(per_traj=True)
+        c64, cp64 = ea.corr(per_traj=True)
+        cmx, cpmx = em.corr(per_traj=True)
+        accuracy = {"n_traj": na, "steps": args.acc_steps, "jumps": jumps,
+                    "max_abs_density_per_traj": float(np.abs(dmx - d64).max()),
+                    "max_abs_density_ensemble": float(np.abs(dmx.mean(0) - d64.mean(0)).max()),
+                    "max_abs_corr_per_traj": float(np.abs(cpmx - cp64).max()),
+                    "max_abs_corr_ensemble": float(np.abs(cmx - c64).max()),
+                    "how": "same start states; the FP64 run samples the jumps, the mixed run "
+                           "replays them"}
+        ea.close()
+        em.close()
+
     # ---- end to end through the public API with host buffers ---------------------------
     e2e = None
     if not args.no_e2e:
@@ -392,6 +426,7 @@ def run_ours(args):
             "jacobi_sweeps_mean": sweeps_mean,
             "fp64_path": fp64,
             "speedup_vs_fp64": (value / world / fp64["updates_per_s"]) if fp64 else None,
+            "mixed_vs_fp64": accuracy,
             "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
