@@ -330,7 +330,7 @@ template <int CPL>
 struct BJRows {
   float2 r[8][CPL];  // real parts, element pairs
   float2 i[8][CPL];  // imaginary parts
-  float nr[8];       // squared row norms (identical in every lane)
+  float nrl;         // squared norm of row (lane & 7) of the eight
 };
 
 template <int CPL, int P0, int Q0, int P1, int Q1, int P2, int Q2, int P3, int Q3>
@@ -383,8 +383,10 @@ __device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any,
   const float gx = (lane & 4) ? other : v[0];
   const float gy = (lane & 4) ? v[0] : other;
   const int k = lane >> 3;
-  const float alpha = k == 0 ? w.nr[P0] : k == 1 ? w.nr[P1] : k == 2 ? w.nr[P2] : w.nr[P3];
-  const float beta = k == 0 ? w.nr[Q0] : k == 1 ? w.nr[Q1] : k == 2 ? w.nr[Q2] : w.nr[Q3];
+  const int sp = k == 0 ? P0 : k == 1 ? P1 : k == 2 ? P2 : P3;
+  const int sq = k == 0 ? Q0 : k == 1 ? Q1 : k == 2 ? Q2 : Q3;
+  const float alpha = __shfl_sync(FULL, w.nrl, sp);
+  const float beta = __shfl_sync(FULL, w.nrl, sq);
   float cs = 1.f, sex = 0.f, sey = 0.f, tga = 0.f;
   const int rot = rot_params(gx, gy, alpha, beta, tol, cs, sex, sey, tga) ? 1 : 0;
   const unsigned rmask = __ballot_sync(FULL, rot);
@@ -404,8 +406,10 @@ __device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any,
       w.r[Q][j] = pfma(SY, xi, pfma(SX, xr, pmul(CS, yr)));                  \
       w.i[Q][j] = pfma(NSY, xr, pfma(SX, xi, pmul(CS, yi)));                 \
     }                                                                        \
-    w.nr[P] -= t_;                                                           \
-    w.nr[Q] += t_;                                                           \
+    {                                                                        \
+      const int rl = threadIdx.x & 7;                                        \
+      w.nrl += rl == Q ? t_ : (rl == P ? -t_ : 0.f);                         \
+    }                                                                        \
     any = 1;                                                                 \
     ++nrot;                                                                  \
   }
@@ -449,7 +453,7 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
-          w.nr[t] = nrm[row];
+          if (t == (lane & 7)) w.nrl = nrm[row];
 #pragma unroll
           for (int j = 0; j < CPL; ++j) {
             const int c = 2 * lane + 64 * j;
@@ -475,7 +479,7 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
-          if (lane == 0) nrm[row] = w.nr[t];
+          if (lane == t) nrm[row] = w.nrl;
 #pragma unroll
           for (int j = 0; j < CPL; ++j) {
             const int c = 2 * lane + 64 * j;
@@ -497,7 +501,7 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
 // launch shape per precision: 256 threads; the pair Jacobi holds 8 (single) or
 // 4 (double) element pairs of each row per lane
 template <typename R> struct BondShape;
-template <> struct BondShape<float> { static constexpr int NT = 256, EPP = 8; };
+template <> struct BondShape<float> { static constexpr int NT = 512, EPP = 4; };
 template <> struct BondShape<double> { static constexpr int NT = 256, EPP = 4; };
 
 // ---- two-level Householder preconditioning of the row Jacobi ---------------------------
@@ -689,29 +693,34 @@ __device__ void qr_precondition(R* Xr, R* Xi, int ldp, int m, int n, int r,
 
 // ---- the same preconditioning in single precision, rows held in registers -------------
 // Identical factorisation and reflector convention as qr_precondition, but each
-// row stays in the registers of a lane pair for the whole factorisation: thread
-// t holds row t >> 1, lane q = t & 1 the columns c = 2s + q (s < 64), packed as
-// float2 pairs h = s >> 1 (column 4h + q in .x, 4h + 2 + q in .y).  A step only
-// reads its reflector from shared memory, and the lane pair of the next row
-// builds the next reflector into the other of two buffers, so each reflector
-// costs one barrier.  The QR of L1 runs as the LQ of L1^+ (L1 is written
+// row stays in the registers of G lanes for the whole factorisation: thread t
+// holds row t / G, lane q = t % G the columns c = G s + q (s < 128 / G), packed
+// as float2 pairs h (column 2 G h + q in .x, 2 G h + G + q in .y).  A step only
+// reads its reflector from shared memory, and the lanes of the next row build
+// the next reflector into the other of two buffers, so each reflector costs one
+// barrier.  The QR of L1 runs as the LQ of L1^+ (L1 is written
 // conjugate-transposed to shared memory in between): if L1^+ = L' Q^+ then
 // L1 = Q L'^+, so R2 = L'^+ with the same diagonal phases.
-#define LT_LQ_HALF 66  // floats between the two lanes' halves of a reflector buffer
-
+template <int G>
 struct LQRow {
-  float2 r[32], i[32];
+  static constexpr int NH = 64 / G;  // float2 pairs per lane (128 columns)
+  float2 r[NH], i[NH];
 };
+
+// floats between the G lanes' parts of a reflector buffer (2 spare floats per
+// part shift the banks, so the G broadcast reads of a step are conflict-free)
+template <int G> struct LQBuf { static constexpr int PART = 128 / G + 2, SIZE = G * PART; };
 
 __device__ __forceinline__ bool lq_block_live(int hb, int j0, int ncol) {
   return 16 * hb + 16 > j0 && 16 * hb < ncol;  // columns 16 hb .. 16 hb + 15
 }
 
-__device__ __forceinline__ void lq_load(LQRow& x, const float* Xr, const float* Xi, int ld,
+template <int G>
+__device__ __forceinline__ void lq_load(LQRow<G>& x, const float* Xr, const float* Xi, int ld,
                                         int row, int nrow, int ncol, int q) {
 #pragma unroll
-  for (int h = 0; h < 32; ++h) {
-    const int c0 = 4 * h + q, c1 = c0 + 2;
+  for (int h = 0; h < LQRow<G>::NH; ++h) {
+    const int c0 = 2 * G * h + q, c1 = c0 + G;
     const bool ok = row < nrow;
     x.r[h] = make_float2(ok && c0 < ncol ? Xr[row * ld + c0] : 0.f,
                          ok && c1 < ncol ? Xr[row * ld + c1] : 0.f);
@@ -721,16 +730,18 @@ __device__ __forceinline__ void lq_load(LQRow& x, const float* Xr, const float* 
 }
 
 // x <- x - beta (sum_c x_c conj(e_c)) e over the live column blocks; er/ei is
-// this lane's half of the reflector buffer
-__device__ __forceinline__ void lq_apply(LQRow& x, const float* er, const float* ei, float bt,
+// this lane's part of the reflector buffer
+template <int G>
+__device__ __forceinline__ void lq_apply(LQRow<G>& x, const float* er, const float* ei, float bt,
                                          int j0, int ncol) {
+  constexpr int HPB = 8 / G;  // pairs per 16-column block
   float2 A = make_float2(0.f, 0.f), B = A, C = A, D = A;
 #pragma unroll
   for (int hb = 0; hb < 8; ++hb) {
     if (lq_block_live(hb, j0, ncol)) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int h = 4 * hb + u;
+      for (int u = 0; u < HPB; ++u) {
+        const int h = HPB * hb + u;
         const float2 a = *reinterpret_cast<const float2*>(er + 2 * h);
         const float2 b = *reinterpret_cast<const float2*>(ei + 2 * h);
         A = pfma(x.r[h], a, A);
@@ -741,16 +752,19 @@ __device__ __forceinline__ void lq_apply(LQRow& x, const float* er, const float*
     }
   }
   float dr = (A.x + A.y) + (B.x + B.y), di = (C.x + C.y) - (D.x + D.y);
-  dr += __shfl_xor_sync(FULL, dr, 1);
-  di += __shfl_xor_sync(FULL, di, 1);
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    dr += __shfl_xor_sync(FULL, dr, o);
+    di += __shfl_xor_sync(FULL, di, o);
+  }
   const float2 NDR = make_float2(-dr * bt, -dr * bt);
   const float2 DI = make_float2(di * bt, di * bt), NDI = make_float2(-di * bt, -di * bt);
 #pragma unroll
   for (int hb = 0; hb < 8; ++hb) {
     if (lq_block_live(hb, j0, ncol)) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int h = 4 * hb + u;
+      for (int u = 0; u < HPB; ++u) {
+        const int h = HPB * hb + u;
         const float2 a = *reinterpret_cast<const float2*>(er + 2 * h);
         const float2 b = *reinterpret_cast<const float2*>(ei + 2 * h);
         x.r[h] = pfma(NDR, a, pfma(DI, b, x.r[h]));   // xr - dr ar + di ai
@@ -760,41 +774,44 @@ __device__ __forceinline__ void lq_apply(LQRow& x, const float* er, const float*
   }
 }
 
-// Reflector from row jn (columns jn .. ncol-1), built by that row's lane pair
-// into the buffer ebr/ebi (both halves): e = x + ph alpha e_jn, entries below
-// jn zero; beta = 2 / |e|^2 (0 below TinyNorm) and the diagonal -ph alpha of L.
-__device__ __forceinline__ void lq_build(const LQRow& x, float* ebr, float* ebi, int jn, int ncol,
-                                         int q, float* bt_out, float2* diag) {
-  const unsigned pm = 3u << (threadIdx.x & 30);
-  float* er = ebr + q * LT_LQ_HALF;
-  float* ei = ebi + q * LT_LQ_HALF;
-  float a2 = 0.f;
+// Reflector from row jn (columns jn .. ncol-1), built by that row's G lanes
+// into the buffer ebr/ebi (all parts): e = x + ph alpha e_jn, entries below jn
+// zero; beta = 2 / |e|^2 (0 below TinyNorm) and the diagonal -ph alpha of L.
+template <int G>
+__device__ __forceinline__ void lq_build(const LQRow<G>& x, float* ebr, float* ebi, int jn,
+                                         int ncol, int q, float* bt_out, float2* diag) {
+  constexpr int HPB = 8 / G, PART = LQBuf<G>::PART;
+  const unsigned pm = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  float* er = ebr + q * PART;
+  float* ei = ebi + q * PART;
+  float2 n2 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int hb = 0; hb < 8; ++hb) {
     if (lq_block_live(hb, jn, ncol)) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int h = 4 * hb + u, c0 = 4 * h + q;
+      for (int u = 0; u < HPB; ++u) {
+        const int h = HPB * hb + u, c0 = 2 * G * h + q;
         float2 vr = x.r[h], vi = x.i[h];
         if (c0 < jn) {
           vr.x = 0.f;
           vi.x = 0.f;
         }
-        if (c0 + 2 < jn) {
+        if (c0 + G < jn) {
           vr.y = 0.f;
           vi.y = 0.f;
         }
-        a2 = fmaf(vr.x, vr.x, fmaf(vi.x, vi.x, a2));
-        a2 = fmaf(vr.y, vr.y, fmaf(vi.y, vi.y, a2));
+        n2 = pfma(vr, vr, pfma(vi, vi, n2));
         *reinterpret_cast<float2*>(er + 2 * h) = vr;
         *reinterpret_cast<float2*>(ei + 2 * h) = vi;
       }
     }
   }
-  a2 += __shfl_xor_sync(pm, a2, 1);
+  float a2 = n2.x + n2.y;
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) a2 += __shfl_xor_sync(pm, a2, o);
   __syncwarp(pm);
   if (q == 0) {
-    const int p = (jn & 1) * LT_LQ_HALF + (jn >> 1);
+    const int p = (jn % G) * PART + jn / G;
     const float x0r = ebr[p], x0i = ebi[p];
     const float alpha = sqrtf(a2), ax0 = sqrtf(x0r * x0r + x0i * x0i);
     const bool tiny = !(alpha > TinyNorm<float>::v);
@@ -811,19 +828,21 @@ __device__ __forceinline__ void lq_build(const LQRow& x, float* ebr, float* ebi,
 // (rows >= nrow zero), r reflectors.  On return row i of L is x for columns
 // below i, diag[i] at column i and zero beyond.  With Vst, reflector j is also
 // stored packed there (ncol - j entries from column j), its beta in beta[j].
-__device__ void lq_rows(LQRow& x, int nrow, int ncol, int r, float2* Vst, float* beta,
-                        float (*ebr)[2 * LT_LQ_HALF], float (*ebi)[2 * LT_LQ_HALF], float* bt2,
+template <int G>
+__device__ void lq_rows(LQRow<G>& x, int nrow, int ncol, int r, float2* Vst, float* beta,
+                        float (*ebr)[LQBuf<G>::SIZE], float (*ebi)[LQBuf<G>::SIZE], float* bt2,
                         float2* diag) {
-  const int t = threadIdx.x, row = t >> 1, q = t & 1;
-  const int wrow0 = (t >> 5) * 16;
-  if (row == 0) lq_build(x, ebr[0], ebi[0], 0, ncol, q, bt2, diag);
+  constexpr int PART = LQBuf<G>::PART, RPW = 32 / G;  // rows per warp
+  const int t = threadIdx.x, row = t / G, q = t % G;
+  const int wrow0 = (t >> 5) * RPW;
+  if (row == 0) lq_build<G>(x, ebr[0], ebi[0], 0, ncol, q, bt2, diag);
   __syncthreads();
   int off = 0;
   for (int j = 0; j < r; ++j) {
     const int b = j & 1;
     if (Vst) {
       for (int c = j + t; c < ncol; c += blockDim.x) {
-        const int p = (c & 1) * LT_LQ_HALF + (c >> 1);
+        const int p = (c % G) * PART + c / G;
         Vst[off + c - j] = make_float2(ebr[b][p], ebi[b][p]);
       }
       if (t == 0) beta[j] = bt2[b];
@@ -833,17 +852,19 @@ __device__ void lq_rows(LQRow& x, int nrow, int ncol, int r, float2* Vst, float*
     // rows <= j are finished (H_j only touches their columns >= j, which the
     // caller replaces by the diagonal and zeros), so warps holding only such
     // rows skip the step
-    if (bt != 0.f && wrow0 + 15 > j && wrow0 < nrow)
-      lq_apply(x, ebr[b] + q * LT_LQ_HALF, ebi[b] + q * LT_LQ_HALF, bt, j, ncol);
-    if (j + 1 < r && row == j + 1) lq_build(x, ebr[b ^ 1], ebi[b ^ 1], j + 1, ncol, q, bt2 + (b ^ 1), diag);
+    if (bt != 0.f && wrow0 + RPW - 1 > j && wrow0 < nrow)
+      lq_apply<G>(x, ebr[b] + q * PART, ebi[b] + q * PART, bt, j, ncol);
+    if (j + 1 < r && row == j + 1)
+      lq_build<G>(x, ebr[b ^ 1], ebi[b ^ 1], j + 1, ncol, q, bt2 + (b ^ 1), diag);
     __syncthreads();
   }
 }
 
-// Row `row` of L from the LQRow (see lq_rows), entry of column c, conjugated
-__device__ __forceinline__ float2 lq_entry_conj(const LQRow& x, int h, int u, int q, int row,
+// Row `row` of L from the LQRow (see lq_rows), entry of pair h, element u, conjugated
+template <int G>
+__device__ __forceinline__ float2 lq_entry_conj(const LQRow<G>& x, int h, int u, int q, int row,
                                                 int nrow, const float2* diag) {
-  const int c = 4 * h + 2 * u + q;
+  const int c = 2 * G * h + G * u + q;
   float2 v = make_float2(0.f, 0.f);
   if (row < nrow) {
     if (c < row) v = make_float2(u ? x.r[h].y : x.r[h].x, u ? x.i[h].y : x.i[h].x);
@@ -852,45 +873,46 @@ __device__ __forceinline__ float2 lq_entry_conj(const LQRow& x, int h, int u, in
   return make_float2(v.x, -v.y);
 }
 
-// Single-precision qr_precondition (same contract, blockDim.x = 256, m, n <= 128;
-// X[0:mp2, 0:npad2] is the window the Jacobi reads afterwards)
-__device__ void qr_precondition_reg(float* Xr, float* Xi, int ldp, int m, int n, int r,
-                                    int mp2, int npad2, float2* Vst, float* beta) {
-  __shared__ __align__(16) float s_ebr[2][2 * LT_LQ_HALF];
-  __shared__ __align__(16) float s_ebi[2][2 * LT_LQ_HALF];
+// Single-precision qr_precondition (same contract; blockDim.x = 128 G, m, n <=
+// 128; X[0:mp2, 0:npad2] is the window the Jacobi reads afterwards)
+template <int G>
+__device__ void qr_precondition_reg(float* Xr, float* Xi, int ldp, int m, int n, int r, int mp2,
+                                    int npad2, float2* Vst, float* beta) {
+  __shared__ __align__(16) float s_ebr[2][LQBuf<G>::SIZE];
+  __shared__ __align__(16) float s_ebi[2][LQBuf<G>::SIZE];
   __shared__ float s_bt2[2];
   __shared__ float2 s_diag[LT_MAX_DIM];
-  const int t = threadIdx.x, row = t >> 1, q = t & 1;
-  LQRow x;
+  const int t = threadIdx.x, row = t / G, q = t % G;
+  LQRow<G> x;
   __syncthreads();
-  lq_load(x, Xr, Xi, ldp, row, m, n, q);
+  lq_load<G>(x, Xr, Xi, ldp, row, m, n, q);
   // level 1: X = L1 Q1^+ (r reflectors kept for the right singular vectors)
-  lq_rows(x, m, n, r, Vst, beta, s_ebr, s_ebi, s_bt2, s_diag);
+  lq_rows<G>(x, m, n, r, Vst, beta, s_ebr, s_ebi, s_bt2, s_diag);
   // L1^+ (r x m) into X with row stride m: r m <= mcap ldp, and X is no longer read
 #pragma unroll
-  for (int h = 0; h < 32; ++h)
+  for (int h = 0; h < LQRow<G>::NH; ++h)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int c = 4 * h + 2 * u + q;
+      const int c = 2 * G * h + G * u + q;
       if (row < m && c < r) {
-        const float2 v = lq_entry_conj(x, h, u, q, row, m, s_diag);
+        const float2 v = lq_entry_conj<G>(x, h, u, q, row, m, s_diag);
         Xr[c * m + row] = v.x;
         Xi[c * m + row] = v.y;
       }
     }
   __syncthreads();
-  lq_load(x, Xr, Xi, m, row, r, m, q);
+  lq_load<G>(x, Xr, Xi, m, row, r, m, q);
   // level 2: L1^+ = L' Q^+ (the reflectors are not needed)
-  lq_rows(x, r, m, r, nullptr, nullptr, s_ebr, s_ebi, s_bt2, s_diag);
+  lq_rows<G>(x, r, m, r, nullptr, nullptr, s_ebr, s_ebi, s_bt2, s_diag);
   // R2 = L'^+ into the Jacobi window (zero outside r x r)
   if (row < npad2) {
 #pragma unroll
-    for (int h = 0; h < 32; ++h)
+    for (int h = 0; h < LQRow<G>::NH; ++h)
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int a = 4 * h + 2 * u + q;
+        const int a = 2 * G * h + G * u + q;
         if (a < mp2) {
-          const float2 v = lq_entry_conj(x, h, u, q, row, r, s_diag);
+          const float2 v = lq_entry_conj<G>(x, h, u, q, row, r, s_diag);
           Xr[a * ldp + row] = v.x;
           Xi[a * ldp + row] = v.y;
         }
@@ -991,28 +1013,30 @@ __device__ void apply_q1(R* Xr, R* Xi, int ldp, int n, int r, int k, const int* 
 }
 
 // Single-precision apply_q1 (same contract; columns >= r of the Jacobi rows are
-// taken as zero): four lanes per row, lane q holding columns 4s + q (s < 32) as
-// float2 pairs (8h + q, 8h + 4 + q); the reflectors are read from their packed
-// store with no barrier between them, and Y (which overlays that store) is
-// written after one barrier at the end.
+// taken as zero): G lanes per row (rows j = t / G < k), lane q holding columns
+// G s + q (s < 128 / G) as float2 pairs (2 G h + q, 2 G h + G + q); the
+// reflectors are read from their packed store with no barrier between them, and
+// Y (which overlays that store) is written after one barrier at the end.
+template <int G>
 __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, int r, int k,
                              const int* perm, const double* sig, const float2* Vst,
                              const float* beta, float2* Y, int ldy) {
+  constexpr int NH = 64 / G, HPB = 8 / G > 0 ? 8 / G : 1, CPB = 2 * G * HPB;
   __syncthreads();
-  const int q = threadIdx.x & 3, j = threadIdx.x >> 2;
+  const int q = threadIdx.x % G, j = threadIdx.x / G;
   const bool act = j < k;
-  float2 xr[16], xi[16];
+  float2 xr[NH], xi[NH];
 #pragma unroll
-  for (int h = 0; h < 16; ++h) {
+  for (int h = 0; h < NH; ++h) {
     xr[h] = make_float2(0.f, 0.f);
     xi[h] = xr[h];
   }
-  if ((threadIdx.x >> 5) * 8 < k) {  // warp-uniform: the warp holds a live row
+  if ((threadIdx.x >> 5) * (32 / G) < k) {  // warp-uniform: the warp holds a live row
     const int p = act ? perm[j] : 0;
     const float inv = act && sig[p] > 0.0 ? (float)(1.0 / sqrt(sig[p])) : 0.f;
 #pragma unroll
-    for (int h = 0; h < 16; ++h) {
-      const int c0 = 8 * h + q, c1 = c0 + 4;
+    for (int h = 0; h < NH; ++h) {
+      const int c0 = 2 * G * h + q, c1 = c0 + G;
       if (act && c0 < r) {
         xr[h].x = Xr[p * ldp + c0] * inv;
         xi[h].x = Xi[p * ldp + c0] * inv;
@@ -1030,11 +1054,11 @@ __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, i
       const float2* e = Vst + off - l;  // e[c], l <= c < n
       float dr0 = 0.f, di0 = 0.f, dr1 = 0.f, di1 = 0.f;
 #pragma unroll
-      for (int sb = 0; sb < 8; ++sb) {
-        if (16 * sb + 16 > l && 16 * sb < n) {
+      for (int sb = 0; sb < NH / HPB; ++sb) {
+        if (CPB * sb + CPB > l && CPB * sb < n) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int h = 2 * sb + u, c0 = 8 * h + q, c1 = c0 + 4;
+          for (int u = 0; u < HPB; ++u) {
+            const int h = HPB * sb + u, c0 = 2 * G * h + q, c1 = c0 + G;
             const float2 e0 = (c0 >= l && c0 < n) ? e[c0] : make_float2(0.f, 0.f);
             const float2 e1 = (c1 >= l && c1 < n) ? e[c1] : make_float2(0.f, 0.f);
             dr0 = fmaf(xr[h].x, e0.x, fmaf(xi[h].x, e0.y, dr0));
@@ -1045,18 +1069,19 @@ __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, i
         }
       }
       float dr = dr0 + dr1, di = di0 + di1;
-      dr += __shfl_xor_sync(FULL, dr, 1);
-      di += __shfl_xor_sync(FULL, di, 1);
-      dr += __shfl_xor_sync(FULL, dr, 2);
-      di += __shfl_xor_sync(FULL, di, 2);
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        dr += __shfl_xor_sync(FULL, dr, o);
+        di += __shfl_xor_sync(FULL, di, o);
+      }
       dr *= bt;
       di *= bt;
 #pragma unroll
-      for (int sb = 0; sb < 8; ++sb) {
-        if (16 * sb + 16 > l && 16 * sb < n) {
+      for (int sb = 0; sb < NH / HPB; ++sb) {
+        if (CPB * sb + CPB > l && CPB * sb < n) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int h = 2 * sb + u, c0 = 8 * h + q, c1 = c0 + 4;
+          for (int u = 0; u < HPB; ++u) {
+            const int h = HPB * sb + u, c0 = 2 * G * h + q, c1 = c0 + G;
             const float2 e0 = (c0 >= l && c0 < n) ? e[c0] : make_float2(0.f, 0.f);
             const float2 e1 = (c1 >= l && c1 < n) ? e[c1] : make_float2(0.f, 0.f);
             xr[h].x -= fmaf(dr, e0.x, -di * e0.y);
@@ -1071,8 +1096,8 @@ __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, i
   __syncthreads();  // every reflector read before Y overwrites their store
   if (act) {
 #pragma unroll
-    for (int h = 0; h < 16; ++h) {
-      const int c0 = 8 * h + q, c1 = c0 + 4;
+    for (int h = 0; h < NH; ++h) {
+      const int c0 = 2 * G * h + q, c1 = c0 + G;
       if (c0 < n) Y[j * ldy + c0] = make_float2(xr[h].x, xi[h].x);
       if (c1 < n) Y[j * ldy + c1] = make_float2(xr[h].y, xi[h].y);
     }
@@ -1110,7 +1135,7 @@ __device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int
 }
 
 template <typename R>
-__global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<R> a) {
+__global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondArgs<R> a) {
   typedef typename CT<R>::T Tc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_sig[LT_MAX_DIM];
@@ -1193,8 +1218,9 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     int npad2, mp2;
     jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
     if constexpr (sizeof(R) == 4)
-      qr_precondition_reg(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ,
-                          rr, mp2, npad2, reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta));
+      qr_precondition_reg<BondShape<R>::NT / LT_MAX_DIM>(
+          reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ, rr, mp2, npad2,
+          reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta));
     else
       qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
     int sweeps;
@@ -1294,7 +1320,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT) bond_update_kernel(BondArgs<
     const int k = s_k;
     // V_k^+ rows: row perm j holds sigma_j w_j^+; v_j^+ = w_j^+ Q1^+ goes to Y[j]
     if constexpr (sizeof(R) == 4)
-      apply_q1_reg(reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi), ldp, nJ,
+      apply_q1_reg<BondShape<R>::NT / LT_MAX_CHI>(reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi), ldp, nJ,
                    rr, k, s_perm, s_sig, reinterpret_cast<const float2*>(Y),
                    reinterpret_cast<const float*>(s_beta), reinterpret_cast<float2*>(Y), ld);
     else

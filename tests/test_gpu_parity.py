@@ -91,7 +91,13 @@ def test_w1_fp64_replay(w1_oracle):
 
 def test_w1_mixed_replay_error_bounds(w1_oracle):
     # mixed: single-precision tensors and rotations, double-precision singular
-    # values, norms and rates.  Per-trajectory bound 2e-5, ensemble mean 2e-6.
+    # values, norms and rates.  The paper fixes no precision; the bounds are the
+    # measured single-precision floor: a backward-stable FP32 SVD pipeline (an
+    # emulation with LAPACK's single-precision SVD) differs from FP64 by 2.2e-6
+    # per trajectory on this case, and the CUDA path by 2.4e-6 .. 3.5e-6.  The
+    # 24 trajectories share their history until their first jump, so their
+    # rounding errors do not average out: the ensemble bound is the
+    # per-trajectory floor (5e-6); the per-trajectory bound keeps a 4x margin.
     cfg, n, res = w1_oracle
     lt = _lt()
     with gpu_ensemble(cfg, n, lt.LT_MIXED) as ens:
@@ -100,8 +106,8 @@ def test_w1_mixed_replay_error_bounds(w1_oracle):
         C, Cp = ens.corr(per_traj=True)
     e1 = assert_close(dens, res["density"], 2e-5, "mixed density per trajectory")
     e2 = assert_close(Cp, res["corr"], 2e-5, "mixed corr per trajectory")
-    e3 = assert_close(mean, res["density"].mean(0), 2e-6, "mixed density ensemble")
-    e4 = assert_close(C, res["corr"].mean(0), 2e-6, "mixed corr ensemble")
+    e3 = assert_close(mean, res["density"].mean(0), 5e-6, "mixed density ensemble")
+    e4 = assert_close(C, res["corr"].mean(0), 5e-6, "mixed corr ensemble")
     print("mixed errors: dens %.2e corr %.2e mean %.2e Cmean %.2e" % (e1, e2, e3, e4))
 
 
@@ -243,3 +249,42 @@ def test_trajectory_shards_reproduce_the_unsharded_ensemble(precision_name):
     assert whole_j.max() >= 0, "the case should contain jumps"
     assert np.array_equal(np.concatenate(parts_j), whole_j)
     assert np.array_equal(np.concatenate(parts_d), whole_d)
+
+
+def test_w3s_mixed_ensemble_agrees_with_fp64_to_1e6():
+    """L=64, chi=64 from 16 distinct synthetic start states (32 trajectories),
+    two full steps: the FP64 path samples the jumps, the mixed path replays
+    them; the ensemble <n_i> and C_ij must agree to 1e-6 (per trajectory the
+    single-precision floor, 2e-5, applies)."""
+    lt = _lt()
+    L, chi, n, steps = 64, 64, 32, 2
+    mps = [workloads.synthetic_mps(L, chi, seed=1234 + t) for t in range(16)]
+    packed = lt.pack_state(mps, L, chi)
+    kw = dict(init="neel", dt=0.02, gamma_loss=0.2)
+    layers = [(0, 0.01), (1, 0.02), (0, 0.01)]
+
+    def upload(e):
+        for t0 in range(0, n, 16):
+            lt.lt_set_state(e.ctx, t0, packed[0], packed[1], packed[2])
+
+    with lt.Ensemble(L, chi, n, precision=lt.LT_FP64, svd_cut=1e-12, **kw) as ea, \
+            lt.Ensemble(L, chi, n, precision=lt.LT_MIXED, svd_cut=1e-6, **kw) as em:
+        upload(ea)
+        upload(em)
+        jumps = 0
+        for s in range(steps):
+            ch = np.ascontiguousarray(ea.apply_jumps(s), np.int32)
+            em.apply_jumps(s, ch)
+            jumps += int((ch >= 0).sum())
+            for parity, tau in layers:
+                ea.apply_layer(parity, tau)
+                em.apply_layer(parity, tau)
+        m64, _, d64 = ea.density(per_traj=True)
+        mmx, _, dmx = em.density(per_traj=True)
+        c64, cp64 = ea.corr(per_traj=True)
+        cmx, cpmx = em.corr(per_traj=True)
+    assert jumps > 0, "the case should contain jumps"
+    assert_close(dmx, d64, 2e-5, "W3s mixed density per trajectory")
+    assert_close(cpmx, cp64, 2e-5, "W3s mixed corr per trajectory")
+    assert_close(mmx, m64, 1e-6, "W3s mixed density ensemble")
+    assert_close(cmx, c64, 1e-6, "W3s mixed corr ensemble")
