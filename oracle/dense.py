@@ -10,6 +10,12 @@ corr_rk4           the closed linear equation of motion of C_ij = <c_i^+ c_j>
 corr_uniform_loss  its closed form for uniform loss gamma and no gain or
                    dephasing: C(t) = exp(-gamma t) U C(0) U^+, U = exp(-i A t),
                    with A = J x adjacency (Eq. SoleqCorr with Gamma = 0).
+dense_qsd          a quantum-state-diffusion history (Sec. 5.2) on the full
+                   vector: the same Trotter layers and noise operators as the
+                   MPS integrator, unnormalised.
+qsd_mean_map       the exact noise average of one QSD step on rho: E[eta] = 0
+                   and E[eta^2] = 1 turn each factor 1 + eta a L into
+                   rho -> rho + a^2 L rho L^+, applied channel by channel.
 Basis index: sum_i s_i 2^(L-1-i) (site 0 most significant).
 """
 import numpy as np
@@ -179,3 +185,58 @@ def corr_uniform_loss(L, J, gamma, C0, t):
     eps = 2.0 * J * np.cos(np.pi * q / (L + 1))
     U = (V * np.exp(-1j * eps * t)) @ V.T
     return np.exp(-gamma * t) * (U @ C0 @ U.conj().T)
+
+
+def _layer_ops(cfg):
+    L = cfg.L
+    ops = []
+    for parity, tau in cfg.layers():
+        gates = cfg.gates(tau)
+        op = np.eye(2 ** L, dtype=complex)
+        for b in range(parity, L - 1, 2):
+            op = bond_op(L, b, gates[b]) @ op
+        ops.append(op)
+    return ops
+
+
+def _qsd_site_factors(cfg, site):
+    """[(a, L_k)] of one site in the order the factors are applied (loss, gain,
+    dephasing), a = sqrt(gamma_k dt); L_k acts on that site only."""
+    gam = (cfg.gamma_loss[site], cfg.gamma_gain[site], cfg.gamma_deph[site])
+    out = []
+    for kind in (model.LOSS, model.GAIN, model.DEPHASING):
+        if gam[kind] > 0:
+            out.append((np.sqrt(gam[kind] * cfg.dt), site_op(cfg.L, site, model.jump_operator(kind))))
+    return out
+
+
+def dense_qsd(cfg, traj_id, n_steps, psi0=None):
+    """Unnormalised QSD history on the full vector with the Philox noise of
+    (traj_id, step); returns psi (its squared norm is the weight w)."""
+    from .philox import noise
+    L = cfg.L
+    layers = _layer_ops(cfg)
+    psi = product_state(L, cfg.occupation) if psi0 is None else psi0.copy()
+    for step in range(n_steps):
+        for op in layers:
+            psi = op @ psi
+        eta = noise(cfg.seed, traj_id, step, 3 * L)
+        for i in range(L):
+            kinds = [k for k, g in ((model.LOSS, cfg.gamma_loss[i]), (model.GAIN, cfg.gamma_gain[i]),
+                                    (model.DEPHASING, cfg.gamma_deph[i])) if g > 0]
+            for kind, (a, Lk) in zip(kinds, _qsd_site_factors(cfg, i)):
+                psi = psi + eta[3 * i + kind] * a * (Lk @ psi)
+    return psi
+
+
+def qsd_mean_map(cfg, rho0, n_steps):
+    """rho_bar after n_steps exact noise-averaged QSD steps (see module doc)."""
+    layers = _layer_ops(cfg)
+    rho = rho0.copy()
+    for _ in range(n_steps):
+        for op in layers:
+            rho = op @ rho @ op.conj().T
+        for i in range(cfg.L):
+            for a, Lk in _qsd_site_factors(cfg, i):
+                rho = rho + a * a * (Lk @ rho @ Lk.conj().T)
+    return rho

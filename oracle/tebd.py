@@ -37,7 +37,7 @@ form only approximately canonical.
 import numpy as np
 
 from . import model
-from .philox import uniform01, PURPOSE_JUMP
+from .philox import uniform01, noise, PURPOSE_JUMP
 
 IDENTITY4 = np.eye(4, dtype=complex)
 
@@ -89,6 +89,7 @@ class Trajectory:
             self.B.append(t)
         self.lam = [np.ones(1) for _ in range(L - 1)]
         self.trunc_weight = 0.0
+        self.log_weight = 0.0   # ln <psi|psi> of the unnormalised QSD state (Sec. 5.2)
 
     @classmethod
     def from_tensors(cls, cfg, B, lam):
@@ -97,6 +98,7 @@ class Trajectory:
         self.B = [np.array(b, dtype=complex) for b in B]
         self.lam = [np.array(x, dtype=float) for x in lam]
         self.trunc_weight = 0.0
+        self.log_weight = 0.0
         return self
 
     def bond_dims(self):
@@ -106,7 +108,10 @@ class Trajectory:
         return self.lam[b - 1] if b > 0 else np.ones(1)
 
     # ---- Sec. 2.3, Eq. Theta (Hastings form) --------------------------------
-    def update_bond(self, b, G):
+    def update_bond(self, b, G, keep_norm=False):
+        """Two-site update.  With keep_norm (quantum state diffusion) B_b keeps
+        the factor ||S_k||, so the represented state carries the norm change of
+        the non-unitary gate; Lambda_b is normalised either way."""
         cfg = self.cfg
         Bl, Br = self.B[b], self.B[b + 1]
         chiL, chiR = Bl.shape[0], Br.shape[2]
@@ -125,12 +130,16 @@ class Trajectory:
         self.trunc_weight += (total - kept) / total
         Vk_h = Vh[:k]
         self.B[b + 1] = Vk_h.reshape(k, 2, chiR).copy()
-        self.B[b] = (tt @ Vk_h.conj().T / norm).reshape(chiL, 2, k)
+        self.B[b] = (tt @ Vk_h.conj().T / (1.0 if keep_norm else norm)).reshape(chiL, 2, k)
         self.lam[b] = S[:k] / norm
 
-    def apply_layer(self, parity, gates):
+    def apply_layer(self, parity, gates, keep_norm=False):
         for b in range(parity, self.cfg.L - 1, 2):
-            self.update_bond(b, gates[b])
+            self.update_bond(b, gates[b], keep_norm)
+
+    def apply_site_operator(self, i, M):
+        """B_i <- M B_i on the physical index (M a 2 x 2 matrix)."""
+        self.B[i] = np.einsum('uv,avc->auc', M, self.B[i])
 
     # ---- expectation values (Fig. 3, with exact environments) ---------------
     def environments(self):
@@ -194,11 +203,17 @@ class Trajectory:
         """Restore the exact canonical form (every B right-canonical, every Lambda
         the Schmidt spectrum of its bond).  The sweep covers the whole chain: the
         effective-Hamiltonian layers before a jump leave the form only
-        approximately canonical on both sides of the jump site."""
+        approximately canonical on both sides of the jump site.  Returns the
+        squared norm the state had (found at bond 0, where everything to the
+        right is right-canonical, and divided out there)."""
         for b in range(self.cfg.L - 2, -1, -1):
             self.shift_left(b)
+        norm2 = 1.0
         for b in range(0, self.cfg.L - 1):
-            self.restore_bond(b)
+            kept = self.restore_bond(b)
+            if b == 0:
+                norm2 = kept
+        return norm2
 
     # ---- moving the orthogonality centre by one-site SVDs (Sec. 2.2, Eq. ShiftCenter)
     def _keep(self, S):
@@ -240,6 +255,7 @@ class Trajectory:
         self.B[b] = (Bm @ Vk_h.conj().T / norm).reshape(chiL, 2, k)
         self.B[b + 1] = (Vk_h @ Br.reshape(chiM, 2 * chiR)).reshape(k, 2, chiR)
         self.lam[b] = S[:k] / norm
+        return kept
 
     # ---- <c_i^+ c_j> by transfer matrices -------------------------------------
     def correlation(self):
@@ -339,6 +355,79 @@ def run_trajectories(cfg, n_steps, traj_ids, replay=None, measure_corr=False,
         trunc[idx] = traj.trunc_weight
         dims[idx] = traj.bond_dims()
     return dict(density=dens, corr=corr, jumps=jumps, trunc=trunc, bond_dims=dims)
+
+
+# ---- quantum state diffusion (Sec. 5.2) -------------------------------------------
+def qsd_check(cfg):
+    """The noise operators 1 + eta sqrt(gamma dt) L_k must act on one site: a
+    loss or gain channel with the Jordan-Wigner string (fermionic c_k for k > 0)
+    would make them sums of non-local products."""
+    if cfg.fermionic and (np.any(cfg.gamma_loss[1:] > 0) or np.any(cfg.gamma_gain[1:] > 0)):
+        raise ValueError("quantum state diffusion needs local jump operators: fermionic "
+                         "loss or gain only on site 0, or spin operators")
+
+
+def qsd_site_operator(cfg, site, eta):
+    """prod_k (1 + eta_k sqrt(gamma_k dt) L_k) over the channels k = 3 site + kind
+    of one site, applied in increasing k (loss, then gain, then dephasing);
+    eta = (eta_loss, eta_gain, eta_deph)."""
+    gam = (cfg.gamma_loss[site], cfg.gamma_gain[site], cfg.gamma_deph[site])
+    M = model.IDENTITY2.copy()
+    for kind in (model.LOSS, model.GAIN, model.DEPHASING):
+        if gam[kind] > 0:
+            a = eta[kind] * np.sqrt(gam[kind] * cfg.dt)
+            M = (model.IDENTITY2 + a * model.jump_operator(kind)) @ M
+    return M
+
+
+def step_qsd(traj, gates, traj_id, step):
+    """One step of the first-order scheme of Sec. 5.2: |psi> <- prod_k (1 +
+    eta_k sqrt(gamma_k dt) L_k) exp(-i H_eff dt) |psi>, with the exponential by the
+    Trotter layers (no renormalisation, so the state keeps its norm change), the
+    noise eta_k from the Philox Gaussian pairs of (trajectory, step), then the
+    exact canonical form; the squared norm removed there multiplies the weight
+    w = <psi|psi> (log_weight += ln)."""
+    cfg = traj.cfg
+    for parity, g in gates.layers:
+        traj.apply_layer(parity, g, keep_norm=True)
+    eta = noise(cfg.seed, traj_id, step, 3 * cfg.L)
+    for i in range(cfg.L):
+        traj.apply_site_operator(i, qsd_site_operator(cfg, i, eta[3 * i:3 * i + 3]))
+    traj.log_weight += float(np.log(traj.recanonicalize()))
+
+
+def run_qsd(cfg, n_steps, traj_ids, measure_corr=False, initial=None):
+    """Integrate the QSD histories traj_ids for n_steps steps.  Returns
+    dict(density [n, L] and corr [n, L, L] of the normalised states, log_weight
+    [n] = ln <psi|psi>, trunc [n], bond_dims [n, L-1])."""
+    qsd_check(cfg)
+    gates = StepGates(cfg)
+    n = len(traj_ids)
+    dens = np.zeros((n, cfg.L))
+    corr = np.zeros((n, cfg.L, cfg.L), dtype=complex) if measure_corr else None
+    logw = np.zeros(n)
+    trunc = np.zeros(n)
+    dims = np.zeros((n, cfg.L - 1), dtype=np.int64)
+    for idx, tid in enumerate(traj_ids):
+        traj = Trajectory(cfg) if initial is None else Trajectory.from_tensors(cfg, *initial[idx])
+        for step in range(n_steps):
+            step_qsd(traj, gates, tid, step)
+        dens[idx] = traj.density()
+        if measure_corr:
+            corr[idx] = traj.correlation()
+        logw[idx] = traj.log_weight
+        trunc[idx] = traj.trunc_weight
+        dims[idx] = traj.bond_dims()
+    return dict(density=dens, corr=corr, log_weight=logw, trunc=trunc, bond_dims=dims)
+
+
+def qsd_estimate(values, log_weight):
+    """Sec. 5.2: the average density matrix is the mean of |psi><psi| over the
+    unnormalised histories, so <O> = mean_t(w_t <O>_t) with w_t = <psi_t|psi_t> and
+    <O>_t the normalised expectation; returns that mean and its CLT error."""
+    w = np.exp(np.asarray(log_weight))
+    x = np.asarray(values) * w.reshape((-1,) + (1,) * (np.ndim(values) - 1))
+    return ensemble_stats(x)
 
 
 def ensemble_stats(values):
