@@ -66,7 +66,7 @@ typedef struct {
   int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 64             */
   int32_t n_traj;            /* trajectories held by this context, >= 1            */
   int32_t kraus_dim;         /* unused by LT_TRAJ (purified method), set 0         */
-  int32_t method;            /* lt_method; only LT_TRAJ is built                   */
+  int32_t method;            /* lt_method; LT_TRAJ and LT_QSD are built            */
   int32_t precision;         /* lt_precision                                       */
   int32_t init;              /* lt_init                                            */
   int32_t trotter_order;     /* 1: A(dt) B(dt); 2: A(dt/2) B(dt) A(dt/2)           */
@@ -118,22 +118,46 @@ lt_status lt_apply_layer(lt_ctx ctx, int32_t parity, double tau);
 lt_status lt_apply_jumps(lt_ctx ctx, int64_t step, const int32_t* replay,
                          int32_t* out_channel);
 
-/* QSD noise (Sec. 4.2): not built, returns LT_ERR_UNSUPPORTED. */
+/* Quantum state diffusion noise of time step `step` (Sec. 5.2, LT_QSD
+ * contexts; LT_ERR_UNSUPPORTED otherwise).  The scheme iterates
+ * |psi> <- prod_k (1 + eta_k sqrt(gamma_k dt) L_k) exp(-i H_eff dt) |psi> on
+ * unnormalised histories: in an LT_QSD context lt_apply_layer keeps the norm
+ * change of its non-unitary gates in the state (B_b <- theta~ V_k, no division
+ * by ||S_k||), and this call then applies on every site the real 2 x 2 matrix
+ * prod over the site's channels (loss, then gain, then dephasing) of
+ * 1 + eta_k sqrt(gamma_k dt) L_k, with eta_k standard normal: eta_{2j} and
+ * eta_{2j+1} are the Box-Muller pair of the Philox4x32-10 draw with counter
+ * (traj_offset + traj, step, 1 + j, step >> 32) and key seed, k = 3 site +
+ * kind.  It then restores the exact canonical form of every history (one-site
+ * SVDs right to left, then left to right) and adds ln <psi|psi>, found at bond
+ * 0, to the history's log weight (lt_get_log_weights).  Only site-local L_k are
+ * accepted: lt_create returns LT_ERR_UNSUPPORTED for an LT_QSD context with
+ * fermionic loss or gain beyond site 0 (the string would make the factor a sum
+ * of non-local products). */
 lt_status lt_apply_noise(lt_ctx ctx, int64_t step);
 
-/* n_steps full time steps: lt_apply_jumps(step, NULL, NULL) then the layers
- * of the configured Trotter order, with step counting on from the context's
- * step counter (starting at 0). */
+/* ln <psi|psi> of every unnormalised QSD history, out: [n_traj] (0 for the
+ * trajectory method and after lt_set_state). */
+lt_status lt_get_log_weights(lt_ctx ctx, double* out);
+
+/* n_steps full time steps with step counting on from the context's step
+ * counter (starting at 0): for LT_TRAJ lt_apply_jumps(step, NULL, NULL) then
+ * the layers of the configured Trotter order; for LT_QSD the layers then
+ * lt_apply_noise(step). */
 lt_status lt_step(lt_ctx ctx, int32_t n_steps);
 
 /* Ensemble density <n_i> = <psi|n_i|psi>/<psi|psi> (exact environments).
  * mean: [L] average over trajectories; sem: [L] CLT error sqrt(var/n_traj)
- * (Eq. ErrorCLT), or NULL; per_traj: [n_traj * L] row-major, or NULL. */
+ * (Eq. ErrorCLT), or NULL; per_traj: [n_traj * L] row-major, or NULL.  For
+ * LT_QSD the ensemble quantities average w_t <n_i>_t with w_t = <psi_t|psi_t>
+ * (the mean of |psi><psi| over unnormalised histories, Sec. 5.2), while
+ * per_traj holds the normalised <n_i>_t. */
 lt_status lt_measure_density(lt_ctx ctx, double* mean, double* sem, double* per_traj);
 
 /* Correlation matrix C_ij = <c_i^+ c_j> (Sec. 2.1) by transfer matrices with
- * the Jordan-Wigner string.  C_re/C_im: [L * L] row-major ensemble mean;
- * per_traj_re/per_traj_im: [n_traj * L * L] or NULL. */
+ * the Jordan-Wigner string.  C_re/C_im: [L * L] row-major ensemble mean
+ * (weighted as for the density in LT_QSD contexts); per_traj_re/per_traj_im:
+ * [n_traj * L * L] normalised, or NULL. */
 lt_status lt_measure_corr(lt_ctx ctx, double* C_re, double* C_im,
                           double* per_traj_re, double* per_traj_im);
 
@@ -146,14 +170,16 @@ lt_status lt_get_stats(lt_ctx ctx, double* trunc_weight, int32_t* bond_dims);
  * B [L * 2 * chi_max^2] complex128 as interleaved (re, im) doubles, site i at
  * i * 2 * chi_max^2, holding B_i[a][s][c] row-major over its actual shape
  * (chi_{i-1}, 2, chi_i).  Dimensions must satisfy 1 <= chi_b <= chi_max.
- * lt_set_state also clears the truncation accumulators of those trajectories. */
+ * lt_set_state also clears the truncation accumulators and the log weights of
+ * those trajectories. */
 lt_status lt_set_state(lt_ctx ctx, int32_t traj0, int32_t n, const int32_t* dims,
                        const double* lam, const double* B);
 lt_status lt_get_state(lt_ctx ctx, int32_t traj0, int32_t n, int32_t* dims,
                        double* lam, double* B);
 
-/* Checkpoint / resume: write or read the whole ensemble, the step counter and
- * the truncation accumulators to or from a file.  Philox draws are keyed by
+/* Checkpoint / resume: write or read the whole ensemble, the step counter, the
+ * truncation accumulators and the log weights to or from a file (format
+ * LTCKPT02; the method, precision and sizes must match the context).  Philox draws are keyed by
  * (trajectory, step), so a resumed run is bit-identical to an uninterrupted one. */
 lt_status lt_save(lt_ctx ctx, const char* path);
 lt_status lt_load(lt_ctx ctx, const char* path);

@@ -152,7 +152,7 @@ template <typename T> lt_status dalloc(lt_ctx_s* c, T** p, size_t n) {
 
 void free_all(lt_ctx_s* c) {
   void* ptrs[] = {c->B, c->lam, c->dims, c->trunc, c->evolve, c->channel, c->replay,
-                  c->active_list, c->jumped_list, c->counts, c->density, c->rates, c->gam,
+                  c->active_list, c->jumped_list, c->counts, c->density, c->logw, c->rates, c->gam,
                   c->err_dev, c->sweep_hist, c->counters, c->gates, c->bond_scratch, c->env_scratch,
                   c->corr, c->red};
   for (void* p : ptrs)
@@ -215,7 +215,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (!out) return LT_ERR_ARG;
   *out = nullptr;
   if (!cfg) return LT_ERR_ARG;
-  if (cfg->method != LT_TRAJ) return LT_ERR_UNSUPPORTED;
+  if (cfg->method != LT_TRAJ && cfg->method != LT_QSD) return LT_ERR_UNSUPPORTED;
   if (cfg->L < 2 || cfg->L > 1024 || cfg->chi_max < 1 || cfg->chi_max > LT_MAX_CHI ||
       cfg->n_traj < 1 || (cfg->precision != LT_FP64 && cfg->precision != LT_MIXED) ||
       (cfg->trotter_order != 1 && cfg->trotter_order != 2) || !(cfg->dt > 0.0) ||
@@ -229,6 +229,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   c->L = L;
   c->chi = cfg->chi_max;
   c->n_traj = cfg->n_traj;
+  c->method = cfg->method;
   c->prec = cfg->precision;
   c->order = cfg->trotter_order;
   c->fermionic = cfg->fermionic_jumps ? 1 : 0;
@@ -250,6 +251,13 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
     if (!(c->gl[i] >= 0.0) || !(c->gg[i] >= 0.0) || !(c->gd[i] >= 0.0)) {
       delete c;
       return LT_ERR_ARG;
+    }
+    // quantum state diffusion applies 1 + eta sqrt(gamma dt) L_k: with the
+    // Jordan-Wigner string (fermionic loss or gain beyond site 0) that is a sum
+    // of non-local products, which the site-local noise step does not cover
+    if (c->method == LT_QSD && c->fermionic && i > 0 && (c->gl[i] > 0.0 || c->gg[i] > 0.0)) {
+      delete c;
+      return LT_ERR_UNSUPPORTED;
     }
   }
   c->occ.assign(L, 0);
@@ -296,6 +304,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (st == LT_OK) st = dalloc(c, &c->jumped_list, nt);
   if (st == LT_OK) st = dalloc(c, &c->counts, 2);
   if (st == LT_OK) st = dalloc(c, &c->density, nt * L);
+  if (st == LT_OK) st = dalloc(c, &c->logw, nt);
   if (st == LT_OK) st = dalloc(c, &c->rates, nt * 3 * L);
   if (st == LT_OK) st = dalloc(c, &c->gam, 3 * (size_t)L);
   if (st == LT_OK) st = dalloc(c, &c->err_dev, 1);
@@ -321,6 +330,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->B, 0, nt * L * c->slot * c->celt, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->lam, 0, nt * nb * c->chi * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->logw, 0, nt * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sweep_hist, 0, 64 * sizeof(int), c->stream);
     if (e == cudaSuccess)
       e = cudaMemsetAsync(c->counters, 0, LT_NCOUNTERS * sizeof(unsigned long long), c->stream);
@@ -366,6 +376,10 @@ lt_status lt_apply_jumps(lt_ctx c, int64_t step, const int32_t* replay, int32_t*
   lt_status st = guard(c);
   if (st != LT_OK) return st;
   if (step < 0) return LT_ERR_ARG;
+  if (c->method != LT_TRAJ) {
+    c->last_error = "jumps belong to the quantum-trajectory method";
+    return LT_ERR_UNSUPPORTED;
+  }
   if (replay) {
     // stage through pageable host memory: the caller's array is consumed before return
     c->replay_host.assign(replay, replay + c->n_traj);
@@ -392,11 +406,29 @@ lt_status lt_apply_jumps(lt_ctx c, int64_t step, const int32_t* replay, int32_t*
   return LT_OK;
 }
 
-lt_status lt_apply_noise(lt_ctx c, int64_t) {
+lt_status lt_apply_noise(lt_ctx c, int64_t step) {
   lt_status st = guard(c);
   if (st != LT_OK) return st;
-  c->last_error = "quantum state diffusion is not built";
-  return LT_ERR_UNSUPPORTED;
+  if (step < 0) return LT_ERR_ARG;
+  if (c->method != LT_QSD) {
+    c->last_error = "the noise step belongs to quantum state diffusion";
+    return LT_ERR_UNSUPPORTED;
+  }
+  LT_CK(launch_qsd_noise(c, step));
+  // exact canonical form of every history (the active list holds all of them:
+  // no jumps are drawn); bond 0 of the left-to-right sweep moves <psi|psi> into
+  // the log weight
+  for (int b = c->L - 2; b >= 0; --b) LT_CK(launch_bond(c, c->active_list, c->counts, b, 1, nullptr, 1));
+  for (int b = 0; b <= c->L - 2; ++b) LT_CK(launch_bond(c, c->active_list, c->counts, b, 1, nullptr, 2));
+  return LT_OK;
+}
+
+lt_status lt_get_log_weights(lt_ctx c, double* out) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (!out) return LT_ERR_ARG;
+  LT_CK(cudaMemcpyAsync(out, c->logw, sizeof(double) * c->n_traj, cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);
 }
 
 lt_status lt_step(lt_ctx c, int32_t n_steps) {
@@ -404,8 +436,10 @@ lt_status lt_step(lt_ctx c, int32_t n_steps) {
   if (st != LT_OK) return st;
   if (n_steps < 0) return LT_ERR_ARG;
   for (int s = 0; s < n_steps; ++s) {
-    st = lt_apply_jumps(c, c->step_counter, nullptr, nullptr);
-    if (st != LT_OK) return st;
+    if (c->method == LT_TRAJ) {
+      st = lt_apply_jumps(c, c->step_counter, nullptr, nullptr);
+      if (st != LT_OK) return st;
+    }
     if (c->order == 1) {
       if ((st = lt_apply_layer(c, 0, c->dt)) != LT_OK) return st;
       if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
@@ -413,6 +447,10 @@ lt_status lt_step(lt_ctx c, int32_t n_steps) {
       if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
       if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
       if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
+    }
+    if (c->method == LT_QSD) {
+      st = lt_apply_noise(c, c->step_counter);
+      if (st != LT_OK) return st;
     }
     c->step_counter++;
   }
@@ -495,6 +533,7 @@ lt_status lt_set_state(lt_ctx c, int32_t traj0, int32_t n, const int32_t* dims, 
   LT_CK(cudaMemcpyAsync(c->dims + (size_t)traj0 * nb, dims, sizeof(int) * n * nb, cudaMemcpyHostToDevice, c->stream));
   LT_CK(cudaMemcpyAsync(c->lam + (size_t)traj0 * nb * c->chi, lam, sizeof(double) * n * nb * c->chi, cudaMemcpyHostToDevice, c->stream));
   LT_CK(cudaMemsetAsync(c->trunc + (size_t)traj0 * nb, 0, sizeof(double) * n * nb, c->stream));
+  LT_CK(cudaMemsetAsync(c->logw + traj0, 0, sizeof(double) * n, c->stream));
   const long long per_traj = (long long)c->L * c->slot;
   const int chunk = 8;
   double* stage = nullptr;
@@ -547,9 +586,10 @@ lt_status lt_save(lt_ctx c, const char* path) {
   if (!path) return LT_ERR_ARG;
   const size_t nb = c->L - 1, nt = c->n_traj;
   std::vector<int> dims(nt * nb);
-  std::vector<double> lam(nt * nb * c->chi), tr(nt * nb);
+  std::vector<double> lam(nt * nb * c->chi), tr(nt * nb), lw(nt);
   std::vector<char> B(nt * c->L * c->slot * c->celt);
   LT_CK(cudaStreamSynchronize(c->stream));
+  LT_CK(cudaMemcpyAsync(lw.data(), c->logw, lw.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LT_CK(cudaMemcpyAsync(dims.data(), c->dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LT_CK(cudaMemcpyAsync(lam.data(), c->lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LT_CK(cudaMemcpyAsync(tr.data(), c->trunc, tr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -557,15 +597,16 @@ lt_status lt_save(lt_ctx c, const char* path) {
   LT_CK(cudaStreamSynchronize(c->stream));
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(c, LT_ERR_ARG, "lt_save", "cannot open file");
-  const char magic[8] = {'L', 'T', 'C', 'K', 'P', 'T', '0', '1'};
-  const int hdr[4] = {c->L, c->chi, c->n_traj, c->prec};
+  const char magic[8] = {'L', 'T', 'C', 'K', 'P', 'T', '0', '2'};
+  const int hdr[5] = {c->L, c->chi, c->n_traj, c->prec, c->method};
   const long long stepc = c->step_counter;
-  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 4, f) == 4 &&
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 5, f) == 5 &&
             std::fwrite(&stepc, sizeof(stepc), 1, f) == 1 &&
             std::fwrite(dims.data(), sizeof(int), dims.size(), f) == dims.size() &&
             std::fwrite(lam.data(), sizeof(double), lam.size(), f) == lam.size() &&
             std::fwrite(tr.data(), sizeof(double), tr.size(), f) == tr.size() &&
-            std::fwrite(B.data(), 1, B.size(), f) == B.size();
+            std::fwrite(B.data(), 1, B.size(), f) == B.size() &&
+            std::fwrite(lw.data(), sizeof(double), lw.size(), f) == lw.size();
   ok = (std::fclose(f) == 0) && ok;
   return ok ? LT_OK : fail(c, LT_ERR_ARG, "lt_save", "short write");
 }
@@ -578,18 +619,20 @@ lt_status lt_load(lt_ctx c, const char* path) {
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(c, LT_ERR_ARG, "lt_load", "cannot open file");
   char magic[8];
-  int hdr[4];
+  int hdr[5];
   long long stepc = 0;
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "LTCKPT01", 8) == 0 &&
-            std::fread(hdr, sizeof(int), 4, f) == 4 && hdr[0] == c->L && hdr[1] == c->chi &&
-            hdr[2] == c->n_traj && hdr[3] == c->prec && std::fread(&stepc, sizeof(stepc), 1, f) == 1;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "LTCKPT02", 8) == 0 &&
+            std::fread(hdr, sizeof(int), 5, f) == 5 && hdr[0] == c->L && hdr[1] == c->chi &&
+            hdr[2] == c->n_traj && hdr[3] == c->prec && hdr[4] == c->method &&
+            std::fread(&stepc, sizeof(stepc), 1, f) == 1;
   std::vector<int> dims(nt * nb);
-  std::vector<double> lam(nt * nb * c->chi), tr(nt * nb);
+  std::vector<double> lam(nt * nb * c->chi), tr(nt * nb), lw(nt);
   std::vector<char> B(nt * c->L * c->slot * c->celt);
   ok = ok && std::fread(dims.data(), sizeof(int), dims.size(), f) == dims.size() &&
        std::fread(lam.data(), sizeof(double), lam.size(), f) == lam.size() &&
        std::fread(tr.data(), sizeof(double), tr.size(), f) == tr.size() &&
-       std::fread(B.data(), 1, B.size(), f) == B.size();
+       std::fread(B.data(), 1, B.size(), f) == B.size() &&
+       std::fread(lw.data(), sizeof(double), lw.size(), f) == lw.size();
   std::fclose(f);
   if (!ok) return fail(c, LT_ERR_ARG, "lt_load", "checkpoint does not match this context");
   for (int d : dims)
@@ -599,6 +642,7 @@ lt_status lt_load(lt_ctx c, const char* path) {
   LT_CK(cudaMemcpyAsync(c->lam, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   LT_CK(cudaMemcpyAsync(c->trunc, tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   LT_CK(cudaMemcpyAsync(c->B, B.data(), B.size(), cudaMemcpyHostToDevice, c->stream));
+  LT_CK(cudaMemcpyAsync(c->logw, lw.data(), lw.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   LT_CK(cudaStreamSynchronize(c->stream));
   c->step_counter = stepc;
   return LT_OK;

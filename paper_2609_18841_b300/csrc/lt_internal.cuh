@@ -77,9 +77,9 @@ __device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_
   x2 = y2;
   x3 = lo0;
 }
-// uniform double in [0,1) for counter (c0, step, purpose, step >> 32) and key seed
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint32_t c0, uint64_t step,
-                                                 uint32_t purpose) {
+// the four output words for counter (c0, step, purpose, step >> 32) and key seed
+__device__ __forceinline__ void philox4(uint64_t seed, uint32_t c0, uint64_t step, uint32_t purpose,
+                                        uint32_t (&x)[4]) {
   uint32_t x0 = c0, x1 = (uint32_t)step, x2 = purpose, x3 = (uint32_t)(step >> 32);
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
@@ -90,7 +90,35 @@ __device__ __forceinline__ double philox_uniform(uint64_t seed, uint32_t c0, uin
     }
     philox_round(x0, x1, x2, x3, k0, k1);
   }
-  return ((double)(x0 >> 5) * 67108864.0 + (double)(x1 >> 6)) * (1.0 / 9007199254740992.0);
+  x[0] = x0;
+  x[1] = x1;
+  x[2] = x2;
+  x[3] = x3;
+}
+// uniform double in [0,1) from 27 bits of hi and 26 bits of lo
+__device__ __forceinline__ double philox_words_uniform(uint32_t hi, uint32_t lo) {
+  return ((double)(hi >> 5) * 67108864.0 + (double)(lo >> 6)) * (1.0 / 9007199254740992.0);
+}
+// uniform double in [0,1) for counter (c0, step, purpose, step >> 32) and key seed
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint32_t c0, uint64_t step,
+                                                 uint32_t purpose) {
+  uint32_t x[4];
+  philox4(seed, c0, step, purpose, x);
+  return philox_words_uniform(x[0], x[1]);
+}
+// the j-th pair of standard normal numbers of (c0, step): Box-Muller (Box and
+// Muller 1958) of the uniforms u1 (words 0, 1) and u2 (words 2, 3) of the draw
+// with purpose 1 + j: r = sqrt(-2 ln(1 - u1)), (r cos 2 pi u2, r sin 2 pi u2)
+__device__ __forceinline__ void philox_gaussian_pair(uint64_t seed, uint32_t c0, uint64_t step,
+                                                     uint32_t j, double& g0, double& g1) {
+  uint32_t x[4];
+  philox4(seed, c0, step, 1u + j, x);
+  const double u1 = philox_words_uniform(x[0], x[1]), u2 = philox_words_uniform(x[2], x[3]);
+  const double r = sqrt(-2.0 * log1p(-u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  g0 = r * cs;
+  g1 = r * sn;
 }
 
 // ---- launch descriptors -----------------------------------------------------------
@@ -118,6 +146,8 @@ template <typename R> struct BondArgs {
   double tol;            // Jacobi threshold, 0 = 4 eps sqrt(n)
   int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
   unsigned long long* counters;  // see lt_get_counters
+  int keep_norm;         // mode 0: B_b keeps the factor ||S_k|| (quantum state diffusion)
+  double* logw;          // mode 2 at bond 0: += ln ||S||^2 per trajectory, or nullptr
 };
 
 struct EnvArgs {
@@ -146,7 +176,7 @@ struct EnvArgs {
 
 // ---- context -------------------------------------------------------------------------
 struct lt_ctx_s {
-  int L, chi, n_traj, prec, order, fermionic, max_sweeps;
+  int L, chi, n_traj, prec, order, fermionic, max_sweeps, method;
   double J, dt, cut, jacobi_tol;
   uint64_t seed;
   long long traj_offset;
@@ -172,6 +202,7 @@ struct lt_ctx_s {
   int* jumped_list;
   int* counts;      // [0] = n_active, [1] = n_jumped
   double* density;
+  double* logw;     // [n_traj] ln <psi|psi> of the unnormalised QSD histories
   double* rates;
   double* gam;      // [3][L]
   int* err_dev;
@@ -206,6 +237,7 @@ cudaError_t launch_bond(lt_ctx_s* c, const int* trajs, const int* n_trajs, int b
 cudaError_t launch_env(lt_ctx_s* c, int decide, long long step, const int* replay);
 cudaError_t launch_jump_apply(lt_ctx_s* c);
 cudaError_t launch_compact(lt_ctx_s* c);
+cudaError_t launch_qsd_noise(lt_ctx_s* c, long long step);
 cudaError_t launch_corr(lt_ctx_s* c);
 cudaError_t launch_reduce_density(lt_ctx_s* c, double* out_mean, double* out_sem);
 cudaError_t launch_reduce_corr(lt_ctx_s* c, double* out);

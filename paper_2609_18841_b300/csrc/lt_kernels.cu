@@ -1332,7 +1332,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       form_theta<R>(Xr, Xi, ldp, nJ, 2 * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL, false);
       __syncthreads();
       const int m = 2 * chiL;
-      const R invn = mode == 0 ? (R)(1.0 / s_norm) : (R)1;
+      const R invn = mode == 0 && !a.keep_norm ? (R)(1.0 / s_norm) : (R)1;
       const int rq = (m + 3) >> 2;
       for (int idx = tid; idx < rq * k; idx += blockDim.x) {
         const int r0 = (idx / k) << 2, j = idx - (idx / k) * k;
@@ -1389,6 +1389,9 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       if (tid == 0) {
         a.dims[(long long)traj * (L - 1) + b] = k;
         if (mode != 1) a.trunc[(long long)traj * (L - 1) + b] += s_wdisc;
+        // after the right-to-left sweep everything right of bond 0 is
+        // right-canonical, so ||S||^2 there is <psi|psi>, divided out here
+        if (mode == 2 && b == 0 && a.logw) a.logw[traj] += 2.0 * log(s_norm);
       }
     }
     __syncthreads();
@@ -1875,15 +1878,19 @@ __global__ void compact_kernel(const int* evolve, const int* channel, int n, int
 }
 
 // ensemble mean and CLT error over trajectories: x [n][M] -> mean [M], sem [M]
-__global__ void reduce_mean_sem_kernel(const double* x, int n, int M, double* mean, double* sem) {
+// (with logw, of w_t x[t] with w_t = exp(logw[t]): the quantum-state-diffusion
+// estimator mean_t(w_t <O>_t) of Sec. 5.2)
+__global__ void reduce_mean_sem_kernel(const double* x, int n, int M, double* mean, double* sem,
+                                       const double* logw) {
   __shared__ double red[32];
   for (int col = blockIdx.x; col < M; col += gridDim.x) {
     double s = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s += x[(long long)t * M + col];
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+      s += x[(long long)t * M + col] * (logw ? exp(logw[t]) : 1.0);
     const double mu = block_sum_double(s, red) / n;
     double v = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const double d = x[(long long)t * M + col] - mu;
+      const double d = x[(long long)t * M + col] * (logw ? exp(logw[t]) : 1.0) - mu;
       v += d * d;
     }
     const double var = block_sum_double(v, red) / n;
@@ -1895,14 +1902,16 @@ __global__ void reduce_mean_sem_kernel(const double* x, int n, int M, double* me
 }
 
 // ensemble mean of a double2 [n][M] array -> interleaved double [M][2]
-__global__ void reduce_mean_c_kernel(const double2* x, int n, int M, double* out) {
+__global__ void reduce_mean_c_kernel(const double2* x, int n, int M, double* out,
+                                     const double* logw) {
   __shared__ double red[32];
   for (int col = blockIdx.x; col < M; col += gridDim.x) {
     double re = 0.0, im = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const double2 v = x[(long long)t * M + col];
-      re += v.x;
-      im += v.y;
+      const double w = logw ? exp(logw[t]) : 1.0;
+      re += w * v.x;
+      im += w * v.y;
     }
     re = block_sum_double(re, red);
     im = block_sum_double(im, red);
@@ -1910,6 +1919,65 @@ __global__ void reduce_mean_c_kernel(const double2* x, int n, int M, double* out
       out[2 * col] = re / n;
       out[2 * col + 1] = im / n;
     }
+  }
+}
+
+// ---- quantum state diffusion noise (Sec. 5.2) ----------------------------------------
+// B_i <- M_i B_i on the physical index of every site of every trajectory, with
+// M_i = prod over the site's channels k = 3 i + kind (loss, then gain, then
+// dephasing) of 1 + eta_k sqrt(gamma_k dt) L_k; eta_{2j}, eta_{2j+1} is the j-th
+// Gaussian pair of (trajectory, step).  M_i is real; one CTA per (trajectory,
+// site), thread 0 builds M_i.
+template <typename R>
+__global__ void __launch_bounds__(128) qsd_noise_kernel(typename CT<R>::T* B, const int* dims, int L,
+                                                        int slot, int n_traj, long long traj_offset,
+                                                        long long step, uint64_t seed,
+                                                        const double* gam, double dt) {
+  typedef typename CT<R>::T Tc;
+  __shared__ double sM[4];
+  const long long ntask = (long long)n_traj * L;
+  for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
+    const int traj = (int)(task / L), i = (int)(task - (long long)traj * L);
+    if (threadIdx.x == 0) {
+      double m00 = 1.0, m01 = 0.0, m10 = 0.0, m11 = 1.0;
+      for (int kind = 0; kind < 3; ++kind) {
+        const double g = gam[kind * L + i];
+        if (!(g > 0.0)) continue;
+        const int k = 3 * i + kind;
+        double e0, e1;
+        philox_gaussian_pair(seed, (uint32_t)(traj_offset + traj), (uint64_t)step, (uint32_t)(k >> 1),
+                             e0, e1);
+        const double a = ((k & 1) ? e1 : e0) * sqrt(g * dt);
+        if (kind == 0) {         // loss |0><1|: row 0 += a row 1
+          m00 += a * m10;
+          m01 += a * m11;
+        } else if (kind == 1) {  // gain |1><0|: row 1 += a row 0
+          m10 += a * m00;
+          m11 += a * m01;
+        } else {                 // dephasing |1><1|: row 1 *= 1 + a
+          m10 += a * m10;
+          m11 += a * m11;
+        }
+      }
+      sM[0] = m00;
+      sM[1] = m01;
+      sM[2] = m10;
+      sM[3] = m11;
+    }
+    __syncthreads();
+    const int* dm = dims + (long long)traj * (L - 1);
+    const int chiL = i == 0 ? 1 : dm[i - 1], chiR = i == L - 1 ? 1 : dm[i];
+    Tc* Bi = B + ((long long)traj * L + i) * slot;
+    const R m00 = (R)sM[0], m01 = (R)sM[1], m10 = (R)sM[2], m11 = (R)sM[3];
+    for (int idx = threadIdx.x; idx < chiL * chiR; idx += blockDim.x) {
+      const int aa = idx / chiR, cc = idx - aa * chiR;
+      Tc* p0 = Bi + aa * 2 * chiR + cc;
+      Tc* p1 = p0 + chiR;
+      const Tc v0 = *p0, v1 = *p1;
+      *p0 = cmk<Tc>(m00 * v0.x + m01 * v1.x, m00 * v0.y + m01 * v1.y);
+      *p1 = cmk<Tc>(m10 * v0.x + m11 * v1.x, m10 * v0.y + m11 * v1.y);
+    }
+    __syncthreads();
   }
 }
 
@@ -2023,6 +2091,8 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.tol = c->jacobi_tol;
   a.sweep_hist = c->sweep_hist;
   a.counters = c->counters;
+  a.keep_norm = c->method == LT_QSD && mode == 0;
+  a.logw = c->method == LT_QSD && mode == 2 ? c->logw : nullptr;
   bond_update_kernel<R><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
@@ -2105,14 +2175,30 @@ cudaError_t launch_compact(lt_ctx_s* c) {
 
 cudaError_t launch_reduce_density(lt_ctx_s* c, double* out_mean, double* out_sem) {
   reduce_mean_sem_kernel<<<c->L, LT_BLOCK, 0, c->stream>>>(c->density, c->n_traj, c->L, out_mean,
-                                                           out_sem);
+                                                           out_sem, c->method == LT_QSD ? c->logw : nullptr);
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_corr(lt_ctx_s* c, double* out) {
   const int M = c->L * c->L;
-  reduce_mean_c_kernel<<<M < 4096 ? M : 4096, LT_BLOCK, 0, c->stream>>>(c->corr, c->n_traj, M, out);
+  reduce_mean_c_kernel<<<M < 4096 ? M : 4096, LT_BLOCK, 0, c->stream>>>(
+      c->corr, c->n_traj, M, out, c->method == LT_QSD ? c->logw : nullptr);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qsd_noise(lt_ctx_s* c, long long step) {
+  const long long ntask = (long long)c->n_traj * c->L;
+  const int grid = (int)(ntask < (long long)c->num_sms * 16 ? ntask : (long long)c->num_sms * 16);
+  if (c->prec == LT_MIXED)
+    qsd_noise_kernel<float><<<grid, 128, 0, c->stream>>>(reinterpret_cast<float2*>(c->B), c->dims, c->L,
+                                                          c->slot, c->n_traj, c->traj_offset, step,
+                                                          c->seed, c->gam, c->dt);
+  else
+    qsd_noise_kernel<double><<<grid, 128, 0, c->stream>>>(reinterpret_cast<double2*>(c->B), c->dims,
+                                                           c->L, c->slot, c->n_traj, c->traj_offset,
+                                                           step, c->seed, c->gam, c->dt);
   c->launches++;
   return cudaGetLastError();
 }

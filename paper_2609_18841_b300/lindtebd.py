@@ -37,6 +37,7 @@ class lt_config(ctypes.Structure):
 
 
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
+           "lt_get_log_weights",
            "lt_step", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
            "lt_status_str", "lt_last_error"]
@@ -53,6 +54,7 @@ def load_library(path=LIB_PATH):
         "lt_apply_layer": ([P, I32, D], I32),
         "lt_apply_jumps": ([P, I64, P, P], I32),
         "lt_apply_noise": ([P, I64], I32),
+        "lt_get_log_weights": ([P, P], I32),
         "lt_step": ([P, I32], I32),
         "lt_measure_density": ([P, P, P, P], I32),
         "lt_measure_corr": ([P, P, P, P, P], I32),
@@ -146,6 +148,12 @@ def lt_apply_jumps(ctx, step, replay=None, n_traj=None, want_channels=False):
 
 def lt_apply_noise(ctx, step):
     _check(_lib.lt_apply_noise(ctx, step), "lt_apply_noise", ctx)
+
+
+def lt_get_log_weights(ctx, n_traj):
+    out = np.empty(n_traj)
+    _check(_lib.lt_get_log_weights(ctx, _ptr(out)), "lt_get_log_weights", ctx)
+    return out
 
 
 def lt_step(ctx, n_steps):
@@ -293,6 +301,12 @@ class Ensemble:
 
     def apply_layer(self, parity, tau):
         lt_apply_layer(self.ctx, parity, tau)
+
+    def apply_noise(self, step):
+        lt_apply_noise(self.ctx, step)
+
+    def log_weights(self):
+        return lt_get_log_weights(self.ctx, self.n_traj)
 
     def density(self, per_traj=False):
         return lt_measure_density(self.ctx, self.L, self.n_traj, per_traj)
