@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--traj", type=int, default=workloads.W3["n_traj"])
     ap.add_argument("--fp64-traj", type=int, default=128)
     ap.add_argument("--acc-traj", type=int, default=32)
+    ap.add_argument("--qsd-traj", type=int, default=1024)
+    ap.add_argument("--qsd-steps", type=int, default=2)
     ap.add_argument("--acc-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -325,6 +327,36 @@ def run_ours(args):
                 "n_traj": n64, "steps": 1}
         e64.close()
 
+    # ---- quantum state diffusion leg (Sec. 5.2), one GPU -------------------------------
+    qsd = None
+    if args.qsd_traj > 0 and rank == 0:
+        Lq, nq, dtq = 128, args.qsd_traj, 0.01
+        mq, pq = state_pool(Lq, chi, POOL, seed=4321)
+        eq = lt.Ensemble(Lq, chi, nq, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
+                         dt=dtq, gamma_loss=0.05, gamma_deph=0.1, fermionic_jumps=0,
+                         svd_cut=1e-6, stream=stream.cuda_stream)
+        upload(lt, eq.ctx, pq, nq)
+        lt.lt_step(eq.ctx, 1)
+        torch.cuda.synchronize()
+        eq.counters(clear=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lt.lt_step(eq.ctx, args.qsd_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cq = eq.counters()
+        sq = a.elapsed_time(b) / 1e3
+        lw = eq.log_weights()
+        qsd = {"workload": "QSD: L=128, chi_max=64, %d histories, dephasing 0.1 and spin loss "
+                           "0.05 on every site, Gaussian noise, dt=0.01, synthetic chi=64 start "
+                           "states, mixed precision" % nq,
+               "updates_per_s": cq["updates"] / sq,
+               "layer_updates_per_s": cq["layer_updates"] / sq,
+               "trajectory_steps_per_s": nq * args.qsd_steps / sq,
+               "ms_per_step": 1e3 * sq / args.qsd_steps, "steps": args.qsd_steps,
+               "log_weight_range": [float(lw.min()), float(lw.max())]}
+        eq.close()
+
     # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
     accuracy = None
     if args.acc_traj > 0 and rank == 0:
@@ -427,6 +459,7 @@ def run_ours(args):
             "fp64_path": fp64,
             "speedup_vs_fp64": (value / world / fp64["updates_per_s"]) if fp64 else None,
             "mixed_vs_fp64": accuracy,
+            "qsd": qsd,
             "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
