@@ -201,6 +201,47 @@ lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear)
  * resets the counters after reading.  out: [6] or NULL. */
 lt_status lt_get_counters(lt_ctx ctx, uint64_t* out, int32_t clear);
 
+/* ---- request server (continuous batching; the paper has no serving layer) ----
+ * A request is one ensemble (an lt_config, method LT_TRAJ or LT_QSD) run for
+ * n_steps time steps.  Each admitted request owns a context and its stream on
+ * the current device, so the steps of all active requests are queued side by
+ * side and the GPU interleaves their kernels; the ensemble stays resident from
+ * admission to retirement.  lt_server_tick (1) admits queued requests in
+ * arrival order while their device footprint fits the budget and fewer than
+ * max_active run (a request whose footprint exceeds the budget finishes with
+ * LT_ERR_OOM), (2) queues one time step for every active request (at most two
+ * in flight each) and (3) retires requests whose last step has completed: the
+ * ensemble density (lt_measure_density) is kept and the context freed.
+ * Results are bit-identical to running the request alone.  Not thread-safe:
+ * one host thread drives a server. */
+typedef struct lt_server_s* lt_server;
+
+/* Device bytes lt_create allocates for cfg on a GPU with num_sms SMs (the
+ * occupancy-dependent scratch grids bounded above): the admission estimate. */
+lt_status lt_context_bytes(const lt_config* cfg, int32_t num_sms, uint64_t* out);
+
+/* Admission rule, host only: how many of the queue head (queued_bytes[0..n_queued))
+ * fit in order under budget and max_active, given used bytes and n_active. */
+lt_status lt_admit_plan(uint64_t budget, uint64_t used, int32_t max_active, int32_t n_active,
+                        const uint64_t* queued_bytes, int32_t n_queued, int32_t* n_admit);
+
+lt_status lt_server_create(uint64_t hbm_budget_bytes, int32_t max_active, lt_server* out);
+lt_status lt_server_destroy(lt_server server);
+/* Queue a request (cfg and its arrays are copied); *out_id identifies it. */
+lt_status lt_server_submit(lt_server server, const lt_config* cfg, int32_t n_steps,
+                           int64_t* out_id);
+/* One scheduling round; the counts after it, each may be NULL. */
+lt_status lt_server_tick(lt_server server, int32_t* n_queued, int32_t* n_active,
+                         int32_t* n_finished);
+/* Result of a finished request: mean and sem [L] as lt_measure_density (NULL
+ * allowed), times [3] = submit, admission and completion in seconds since the
+ * server was created.  LT_ERR_STATE while it runs; the request's own status if
+ * it failed (times are still written). */
+lt_status lt_server_result(lt_server server, int64_t id, double* mean, double* sem,
+                           double* times);
+/* Device bytes held by active requests, and the budget. */
+lt_status lt_server_usage(lt_server server, uint64_t* used_bytes, uint64_t* budget_bytes);
+
 /* Allocation-free variant of the per-trajectory density measurement, for
  * callers that cannot call cudaMalloc: processes whose device memory is owned
  * by another allocator (a framework's caching allocator, or a serving runtime

@@ -147,6 +147,7 @@ template <typename T> lt_status dalloc(lt_ctx_s* c, T** p, size_t n) {
     *p = nullptr;
     return fail(c, LT_ERR_OOM, "cudaMalloc", cudaGetErrorString(e));
   }
+  c->dev_bytes += n * sizeof(T);
   return LT_OK;
 }
 
@@ -339,7 +340,10 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_create", cudaGetErrorString(e));
   }
-  if (occ_dev) cudaFree(occ_dev);
+  if (occ_dev) {
+    cudaFree(occ_dev);
+    c->dev_bytes -= L;
+  }
   if (st != LT_OK) {
     free_all(c);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -547,6 +551,7 @@ lt_status lt_set_state(lt_ctx c, int32_t traj0, int32_t n, const int32_t* dims, 
     if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_set_state", cudaGetErrorString(e));
   }
   cudaFree(stage);
+  c->dev_bytes -= 2 * (size_t)per_traj * chunk * sizeof(double);
   return st;
 }
 
@@ -575,6 +580,7 @@ lt_status lt_get_state(lt_ctx c, int32_t traj0, int32_t n, int32_t* dims, double
     if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "lt_get_state", cudaGetErrorString(e));
   }
   cudaFree(stage);
+  c->dev_bytes -= 2 * (size_t)per_traj * chunk * sizeof(double);
   return st;
 }
 

@@ -227,6 +227,7 @@ struct lt_ctx_s {
 
   long long step_counter;
   long long launches;
+  size_t dev_bytes;   // device memory this context allocated
   bool poisoned;
   std::string last_error;
 };

@@ -40,7 +40,9 @@ EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_ap
            "lt_get_log_weights",
            "lt_step", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
-           "lt_status_str", "lt_last_error"]
+           "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
+           "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
+           "lt_server_result", "lt_server_usage"]
 
 
 def load_library(path=LIB_PATH):
@@ -70,6 +72,14 @@ def load_library(path=LIB_PATH):
         "lt_stream": ([P], P),
         "lt_get_step": ([P], I64),
         "lt_status_str": ([I32], ctypes.c_char_p),
+        "lt_context_bytes": ([ctypes.POINTER(lt_config), I32, P], I32),
+        "lt_admit_plan": ([ctypes.c_uint64, ctypes.c_uint64, I32, I32, P, I32, P], I32),
+        "lt_server_create": ([ctypes.c_uint64, I32, ctypes.POINTER(P)], I32),
+        "lt_server_destroy": ([P], I32),
+        "lt_server_submit": ([P, ctypes.POINTER(lt_config), I32, P], I32),
+        "lt_server_tick": ([P, P, P, P], I32),
+        "lt_server_result": ([P, I64, P, P, P], I32),
+        "lt_server_usage": ([P, P, P], I32),
         "lt_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -107,11 +117,11 @@ def _arr(x, L, dtype=np.float64):
     return np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype), (L,)))
 
 
-def lt_create(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.05,
-              trotter_order=2, gamma_loss=None, gamma_gain=None, gamma_deph=None,
-              fermionic_jumps=1, svd_cut=1e-12, seed=0, traj_offset=0, product_occ=None,
-              method=LT_TRAJ, stream=None, max_sweeps=0, jacobi_tol=0.0):
-    """Create a context; returns (handle, keepalive) -- keep both until lt_destroy."""
+def make_config(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.05,
+                trotter_order=2, gamma_loss=None, gamma_gain=None, gamma_deph=None,
+                fermionic_jumps=1, svd_cut=1e-12, seed=0, traj_offset=0, product_occ=None,
+                method=LT_TRAJ, max_sweeps=0, jacobi_tol=0.0):
+    """An lt_config and the arrays it points to (keep both alive while it is used)."""
     cfg = lt_config()
     cfg.L, cfg.chi_max, cfg.n_traj = L, chi_max, n_traj
     cfg.kraus_dim, cfg.method, cfg.precision = 0, method, precision
@@ -124,6 +134,12 @@ def lt_create(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.05
     cfg.fermionic_jumps, cfg.svd_cut = int(fermionic_jumps), svd_cut
     cfg.seed, cfg.traj_offset = seed, traj_offset
     cfg.max_sweeps, cfg.jacobi_tol = max_sweeps, jacobi_tol
+    return cfg, keep
+
+
+def lt_create(L, chi_max, n_traj, stream=None, **kw):
+    """Create a context (keyword arguments as make_config)."""
+    cfg, keep = make_config(L, chi_max, n_traj, **kw)
     h = ctypes.c_void_p()
     _check(_lib.lt_create(ctypes.byref(cfg), stream, ctypes.byref(h)), "lt_create")
     return h
@@ -332,3 +348,74 @@ class Ensemble:
 
     def sweep_histogram(self, clear=False):
         return lt_get_sweep_histogram(self.ctx, clear)
+
+
+# ---- request server ------------------------------------------------------------------
+def lt_context_bytes(L, chi_max, n_traj, num_sms, **kw):
+    cfg, keep = make_config(L, chi_max, n_traj, **kw)
+    out = np.zeros(1, np.uint64)
+    _check(_lib.lt_context_bytes(ctypes.byref(cfg), num_sms, _ptr(out)), "lt_context_bytes")
+    return int(out[0])
+
+
+def lt_admit_plan(budget, used, max_active, n_active, queued_bytes):
+    q = np.ascontiguousarray(queued_bytes, np.uint64)
+    k = np.zeros(1, np.int32)
+    _check(_lib.lt_admit_plan(budget, used, max_active, n_active, _ptr(q), len(q), _ptr(k)),
+           "lt_admit_plan")
+    return int(k[0])
+
+
+class Server:
+    """Continuous-batching request server (include/lindtebd.h, lt_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64):
+        h = ctypes.c_void_p()
+        _check(_lib.lt_server_create(int(hbm_budget_bytes), max_active, ctypes.byref(h)),
+               "lt_server_create")
+        self.h = h
+        self.L = {}
+
+    def submit(self, n_steps, L, chi_max, n_traj, **kw):
+        cfg, keep = make_config(L, chi_max, n_traj, **kw)
+        rid = np.zeros(1, np.int64)
+        _check(_lib.lt_server_submit(self.h, ctypes.byref(cfg), n_steps, _ptr(rid)),
+               "lt_server_submit")
+        self.L[int(rid[0])] = L
+        return int(rid[0])
+
+    def tick(self):
+        c = np.zeros(3, np.int32)
+        _check(_lib.lt_server_tick(self.h, _ptr(c[0:]), _ptr(c[1:]), _ptr(c[2:])), "lt_server_tick")
+        return int(c[0]), int(c[1]), int(c[2])
+
+    def result(self, rid):
+        """(status, mean, sem, times) of a finished request; status LT_ERR_STATE while it runs."""
+        L = self.L[rid]
+        mean, sem, t = np.empty(L), np.empty(L), np.empty(3)
+        st = _lib.lt_server_result(self.h, rid, _ptr(mean), _ptr(sem), _ptr(t))
+        return st, mean, sem, t
+
+    def usage(self):
+        u = np.zeros(2, np.uint64)
+        _check(_lib.lt_server_usage(self.h, _ptr(u[0:]), _ptr(u[1:])), "lt_server_usage")
+        return int(u[0]), int(u[1])
+
+    def run(self, max_ticks=1_000_000):
+        """Tick until nothing is queued or active; returns the tick count."""
+        for n in range(max_ticks):
+            q, a, _ = self.tick()
+            if q == 0 and a == 0:
+                return n + 1
+        raise RuntimeError("server did not drain")
+
+    def close(self):
+        if self.h is not None:
+            _lib.lt_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
