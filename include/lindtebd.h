@@ -239,6 +239,9 @@ lt_status lt_server_tick(lt_server server, int32_t* n_queued, int32_t* n_active,
  * it failed (times are still written). */
 lt_status lt_server_result(lt_server server, int64_t id, double* mean, double* sem,
                            double* times);
+/* Why a finished request failed (the failing call and the CUDA message), "" if
+ * it succeeded or is unknown; valid until the server is destroyed. */
+const char* lt_server_error(lt_server server, int64_t id);
 /* Device bytes held by active requests, and the budget. */
 lt_status lt_server_usage(lt_server server, uint64_t* used_bytes, uint64_t* budget_bytes);
 

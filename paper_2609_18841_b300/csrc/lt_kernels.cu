@@ -2247,15 +2247,19 @@ cudaError_t configure_bond(lt_ctx_s* c) {
   c->bond_smem = c->bond_use_smem ? need : 0;
   cudaError_t e;
   int occ = 0;
+  // The dynamic shared-memory ceiling is a property of the kernel, shared by
+  // every context in the process: it is raised to the most any context may
+  // request (limit), never lowered to one context's need, so contexts of
+  // different chi_max can live side by side.
   if (c->prec == LT_MIXED) {
     e = cudaFuncSetAttribute(bond_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)c->bond_smem);
+                             (int)limit);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<float>,
                                                       BondShape<float>::NT, c->bond_smem);
   } else {
     e = cudaFuncSetAttribute(bond_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)c->bond_smem);
+                             (int)limit);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<double>,
                                                       BondShape<double>::NT, c->bond_smem);

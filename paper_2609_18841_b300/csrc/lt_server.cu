@@ -36,7 +36,8 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
   std::vector<double> mean, sem;
   lt_status status = LT_OK;
-  int state = 0;  // 0 queued, 1 active, 2 finished (status tells success)
+  std::string error;  // the context's last error when the request failed
+  int state = 0;      // 0 queued, 1 active, 2 finished (status tells success)
 };
 
 }  // namespace
@@ -80,6 +81,10 @@ void retire(lt_server_s* s, Request& r, lt_status st) {
   if (r.last) cudaEventDestroy(r.last);
   r.last = nullptr;
   if (r.ctx) {
+    if (st != LT_OK) {
+      const char* e = lt_last_error(r.ctx);
+      r.error = e ? e : "";
+    }
     s->used -= r.bytes;
     lt_destroy(r.ctx);
     r.ctx = nullptr;
@@ -270,6 +275,12 @@ lt_status lt_server_result(lt_server s, int64_t id, double* mean, double* sem, d
   if (mean) std::memcpy(mean, r.mean.data(), sizeof(double) * r.cfg.L);
   if (sem) std::memcpy(sem, r.sem.data(), sizeof(double) * r.cfg.L);
   return LT_OK;
+}
+
+const char* lt_server_error(lt_server s, int64_t id) {
+  if (!s) return "";
+  auto it = s->reqs.find(id);
+  return it == s->reqs.end() ? "" : it->second.error.c_str();
 }
 
 lt_status lt_server_usage(lt_server s, uint64_t* used_bytes, uint64_t* budget_bytes) {

@@ -42,7 +42,7 @@ EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_ap
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
            "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
-           "lt_server_result", "lt_server_usage"]
+           "lt_server_result", "lt_server_error", "lt_server_usage"]
 
 
 def load_library(path=LIB_PATH):
@@ -80,6 +80,7 @@ def load_library(path=LIB_PATH):
         "lt_server_tick": ([P, P, P, P], I32),
         "lt_server_result": ([P, I64, P, P, P], I32),
         "lt_server_usage": ([P, P, P], I32),
+        "lt_server_error": ([P, I64], ctypes.c_char_p),
         "lt_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -395,6 +396,9 @@ class Server:
         mean, sem, t = np.empty(L), np.empty(L), np.empty(3)
         st = _lib.lt_server_result(self.h, rid, _ptr(mean), _ptr(sem), _ptr(t))
         return st, mean, sem, t
+
+    def error(self, rid):
+        return _lib.lt_server_error(self.h, rid).decode()
 
     def usage(self):
         u = np.zeros(2, np.uint64)

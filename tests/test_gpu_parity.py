@@ -288,3 +288,25 @@ def test_w3s_mixed_ensemble_agrees_with_fp64_to_1e6():
     assert_close(cpmx, cp64, 2e-5, "W3s mixed corr per trajectory")
     assert_close(mmx, m64, 1e-6, "W3s mixed density ensemble")
     assert_close(cmx, c64, 1e-6, "W3s mixed corr ensemble")
+
+
+def test_contexts_of_different_chi_live_side_by_side():
+    """The bond kernel's shared-memory ceiling is shared by all contexts of a
+    process: creating a small-chi context must not break a live large-chi one."""
+    lt = _lt()
+    cfg_big = oracle_cfg(workloads.W1, L=12, chi=32)
+    with gpu_ensemble(cfg_big, 4, lt.LT_MIXED) as big:
+        gpu_steps(big, cfg_big, 3)
+        cfg_small = oracle_cfg(workloads.W1, L=8, chi=4)
+        with gpu_ensemble(cfg_small, 2, lt.LT_MIXED) as small:
+            gpu_steps(small, cfg_small, 2)
+            gpu_steps(big, cfg_big, 3, step0=3)
+            gpu_steps(small, cfg_small, 2, step0=2)
+            d_small = small.density(per_traj=True)[2]
+        d_big = big.density(per_traj=True)[2]
+    with gpu_ensemble(cfg_big, 4, lt.LT_MIXED) as ref:
+        gpu_steps(ref, cfg_big, 6)
+        assert np.array_equal(ref.density(per_traj=True)[2], d_big)
+    with gpu_ensemble(cfg_small, 2, lt.LT_MIXED) as ref:
+        gpu_steps(ref, cfg_small, 4)
+        assert np.array_equal(ref.density(per_traj=True)[2], d_small)

@@ -53,6 +53,25 @@ def test_requests_served_together_equal_each_alone():
         assert t[0] <= t[1] <= t[2]
 
 
+def test_staggered_arrivals_of_different_chi():
+    """Requests admitted while others run (a large-chi request first, smaller ones
+    arriving during it) all finish with the results they give alone."""
+    from paper_2609_18841_b300 import lindtebd as lt
+    order = [3, 0, 2, 1]
+    alone = {i: _alone(lt, REQUESTS[i]) for i in order}
+    with lt.Server(8 << 30, 16) as s:
+        ids = {}
+        for i in order:
+            ids[i] = s.submit(**REQUESTS[i])
+            s.tick()
+            s.tick()
+        s.run()
+        for i in order:
+            st, mean, sem, _ = s.result(ids[i])
+            assert st == lt.LT_OK, s.error(ids[i])
+            assert np.array_equal(mean, alone[i][0]) and np.array_equal(sem, alone[i][1])
+
+
 def test_admission_cap_estimate_and_oversize():
     from paper_2609_18841_b300 import lindtebd as lt
     sizes = [lt.lt_context_bytes(r["L"], r["chi_max"], r["n_traj"], num_sms=148,
