@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--acc-traj", type=int, default=32)
     ap.add_argument("--qsd-traj", type=int, default=1024)
     ap.add_argument("--qsd-steps", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--acc-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -357,6 +360,56 @@ def run_ours(args):
                "log_weight_range": [float(lw.min()), float(lw.max())]}
         eq.close()
 
+    # ---- serving: Poisson arrivals of mixed requests through the request server --------
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        rng = np.random.default_rng(77)
+        n_req, rate = args.serve_requests, args.serve_rate
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        reqs = []
+        for i in range(n_req):
+            qsd_req = bool(rng.integers(2))
+            kw = dict(n_steps=int(rng.integers(10, 31)), L=int(rng.choice([16, 32, 64])),
+                      chi_max=int(rng.choice([16, 32, 64])), n_traj=int(rng.choice([1, 8, 32, 128])),
+                      precision=lt.LT_MIXED, method=lt.LT_QSD if qsd_req else lt.LT_TRAJ,
+                      dt=0.02, seed=100 + i, svd_cut=1e-6, init="neel")
+            if qsd_req:
+                kw.update(gamma_deph=0.1, gamma_loss=0.05, fermionic_jumps=0)
+            else:
+                kw.update(gamma_loss=0.1)
+            reqs.append(kw)
+        failed = {}
+        with lt.Server(args.serve_budget_gb << 30, 64) as srv:
+            ids, k = [], 0
+            t0 = time.perf_counter()
+            while True:
+                now = time.perf_counter() - t0
+                while k < n_req and arrivals[k] <= now:
+                    ids.append(srv.submit(**reqs[k]))
+                    k += 1
+                q, a, _ = srv.tick()
+                if k == n_req and q == 0 and a == 0:
+                    break
+                if q == 0 and a == 0:
+                    time.sleep(max(0.0, min(0.002, arrivals[k] - now)))
+            wall = time.perf_counter() - t0
+            lat = []
+            for rid in ids:
+                st, _, _, t = srv.result(rid)
+                if st == lt.LT_OK:
+                    lat.append(t[2] - t[0])
+                else:
+                    failed[str(rid)] = srv.error(rid) or "status %d" % st
+        serving = {"requests": n_req, "completed": len(lat), "failed": failed,
+                   "arrival_rate_per_s": rate, "wall_s": wall,
+                   "completed_per_s": len(lat) / wall,
+                   "latency_s": {"p50": float(np.percentile(lat, 50)),
+                                 "p99": float(np.percentile(lat, 99))} if lat else None,
+                   "mix": "trajectory or QSD (1:1), L in {16,32,64}, chi_max in {16,32,64}, "
+                          "1..128 trajectories, 10..30 steps of dt=0.02, mixed precision, "
+                          "Neel start; Poisson arrivals; latency from submission to completion",
+                   "budget_gb": args.serve_budget_gb}
+
     # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
     accuracy = None
     if args.acc_traj > 0 and rank == 0:
@@ -460,6 +513,7 @@ def run_ours(args):
             "speedup_vs_fp64": (value / world / fp64["updates_per_s"]) if fp64 else None,
             "mixed_vs_fp64": accuracy,
             "qsd": qsd,
+            "serving": serving,
             "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
