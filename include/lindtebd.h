@@ -195,10 +195,14 @@ lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear)
  * operations of the updates in Trotter layers, out[4] the same for the
  * identity-gate updates that restore the canonical form after jumps,
  * out[5] two-site updates executed in Trotter layers.  The operation count of
- * one update with theta of m x n, middle dimension chi_M, k kept values and s
- * sweeps is 8 m n (chi_M + 4) + 4 m n (s + 1) + 8 n P + 24 n Rot + 8 m k n,
- * P = s m (m - 1) / 2 inner products and Rot applied rotations.  clear != 0
- * resets the counters after reading.  out: [6] or NULL. */
+ * one update with theta of m x n, middle dimension chi_M, r = min(m, n), k kept
+ * values and s Jacobi sweeps on the r x r preconditioned factor is
+ * 4 r^2 (s + 1) + 8 r P + 24 r Rot (P = s r (r - 1) / 2 inner products, Rot
+ * applied rotations) + 16 sum_{j<r} [(m-j-1)(n-j) + (m-j)(r-j-1) + k (n-j)]
+ * (the Householder LQ, the QR and the application of Q1) + 8 m n (chi_M + 4) +
+ * 8 m k n (theta and theta~ V_k; the one-site steps count their own
+ * contractions).  clear != 0 resets the counters after reading.  out: [6] or
+ * NULL. */
 lt_status lt_get_counters(lt_ctx ctx, uint64_t* out, int32_t clear);
 
 /* ---- request server (continuous batching; the paper has no serving layer) ----

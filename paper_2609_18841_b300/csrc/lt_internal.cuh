@@ -143,7 +143,7 @@ template <typename R> struct BondArgs {
   long long scratch_stride;
   int use_smem;
   int max_sweeps;
-  double tol;            // Jacobi threshold, 0 = 4 eps sqrt(n)
+  double tol;            // Jacobi threshold, 0 = eps sqrt(n) of the working precision
   int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
   unsigned long long* counters;  // see lt_get_counters
   int keep_norm;         // mode 0: B_b keeps the factor ||S_k|| (quantum state diffusion)

@@ -3,13 +3,17 @@
 //  bond_update_kernel  the two-site update of Sec. 2.3 (Eq. Theta) in
 //                      Vidal-Hastings form, one (trajectory, bond) task per CTA
 //                      iteration: theta formation with the gate fused, a
-//                      one-sided (Hestenes) Jacobi SVD on the rows of theta,
-//                      truncation to chi_max (Sec. 2.2), renormalisation and the
-//                      split B_b <- theta~ V_k / ||S_k||, B_{b+1} <- V_k^+.
-//  env_kernel          exact <n_k> by left/right environments, jump rates
-//                      W_k = gamma_k <L_k^+ L_k> (Eq. TransitionRate) and the
-//                      Philox jump-or-evolve decision (Sec. 4.1).
+//                      two-level Householder preconditioning and a one-sided
+//                      (Hestenes) block Jacobi SVD, truncation to chi_max
+//                      (Sec. 2.2), renormalisation and the split
+//                      B_b <- theta~ V_k / ||S_k||, B_{b+1} <- V_k^+; modes 1 and
+//                      2 are the one-site SVDs that restore the canonical form.
+//  env_tiled_kernel    exact <n_k> by left/right environments (tiled complex
+//                      GEMMs), jump rates W_k = gamma_k <L_k^+ L_k> (Eq.
+//                      TransitionRate) and the Philox jump-or-evolve decision
+//                      (Sec. 4.1).
 //  jump_apply_kernel   L_k on site k and the Jordan-Wigner string on j < k.
+//  qsd_noise_kernel    the quantum-state-diffusion noise factors (Sec. 5.2).
 //  corr_kernel         C_ij = <c_i^+ c_j> by transfer matrices.
 #include <cfloat>
 #include <cstdio>
@@ -1499,58 +1503,6 @@ __device__ void decide_channel(const EnvArgs& a, int traj) {
   a.evolve[traj] = ch < 0 ? 1 : 0;
 }
 
-// env_kernel: per trajectory, exact <n_k> for every site, rates and decision
-// (kRates = false: densities only).
-template <typename R, bool kRates = true>
-__global__ void __launch_bounds__(LT_BLOCK) env_kernel(EnvArgs a) {
-  typedef typename CT<R>::T Tc;
-  __shared__ double red[32];
-  const int L = a.L, chi = a.chi, chi2 = chi * chi;
-  Tc* ws = reinterpret_cast<Tc*>(a.scratch) + (long long)blockIdx.x * a.scratch_stride;
-  Tc* Rl = ws;                                  // (L+1) chi^2
-  Tc* T = Rl + (long long)(L + 1) * chi2;       // chi^2
-  Tc* Le = T + chi2;                            // chi^2
-  Tc* Ln = Le + chi2;                           // chi^2
-  Tc* M0 = Ln + chi2;
-  Tc* M1 = M0 + chi2;
-  Tc* N1 = M1 + chi2;
-  for (int traj = blockIdx.x; traj < a.n_traj; traj += gridDim.x) {
-    const Tc* B = reinterpret_cast<const Tc*>(a.B) + (long long)traj * L * a.slot;
-    const int* dm = a.dims + (long long)traj * (L - 1);
-    const double nrm2 = right_envs<R>(B, dm, L, chi, a.slot, Rl, T);
-    if (threadIdx.x == 0) Le[0] = cmk<Tc>(1.0, 0.0);
-    __syncthreads();
-    for (int k = 0; k < L; ++k) {
-      const int cl = k == 0 ? 1 : dm[k - 1], cr = k == L - 1 ? 1 : dm[k];
-      const Tc* Bk = B + (long long)k * a.slot;
-      bgemm<R>(cl, cr, cl, Le, chi, 0, Bk + cr, 2 * cr, 0, M1, chi, 0, (R)1);
-      bgemm<R>(cl, cr, cl, Le, chi, 0, Bk, 2 * cr, 0, M0, chi, 0, (R)1);
-      __syncthreads();
-      bgemm<R>(cl, cr, cr, M1, chi, 0, Rl + (long long)(k + 1) * chi2, chi, 0, N1, chi, 0, (R)1);
-      bgemm<R>(cr, cr, cl, Bk, 2 * cr, 1, M0, chi, 0, Ln, chi, 0, (R)1);
-      __syncthreads();
-      bgemm<R>(cr, cr, cl, Bk + cr, 2 * cr, 1, M1, chi, 0, Ln, chi, 1, (R)1);
-      const double2 d = block_cdot<R>(cl, cr, Bk + cr, 2 * cr, N1, chi, red);
-      if (threadIdx.x == 0) {
-        const double nk = d.x / nrm2;
-        a.density[(long long)traj * L + k] = nk;
-        if (kRates) {
-          double* rt = a.rates + (long long)traj * 3 * L + 3 * k;
-          rt[0] = a.gl[k] * nk;
-          rt[1] = a.gg[k] * (1.0 - nk);
-          rt[2] = a.gd[k] * nk;
-        }
-      }
-      __syncthreads();
-      Tc* tmp = Le;
-      Le = Ln;
-      Ln = tmp;
-    }
-    if (kRates && a.decide && threadIdx.x == 0) decide_channel(a, traj);
-    __syncthreads();
-  }
-}
-
 // ---- shared-memory tiled complex GEMM (one CTA of 256 threads) -----------------------
 // C (M x N) = (acc ? C : 0) + op(A) op(B), where op(A)(i,k) = A[i ar + k ac] and
 // op(B)(k,j) = B[k br + j bc], each conjugated when its flag is set.  Output
@@ -1664,7 +1616,7 @@ __device__ double right_envs_tiled(const typename CT<R>::T* B, const int* dm, in
 }
 
 // env kernel with tiled contractions: per trajectory exact <n_k> for every
-// site, then (kRates) rates and the Philox decision as in env_kernel
+// site, then (kRates) rates and the Philox decision (decide_channel)
 template <typename R, bool kRates = true>
 __global__ void __launch_bounds__(LT_BLOCK) env_tiled_kernel(EnvArgs a) {
   typedef typename CT<R>::T Tc;
