@@ -185,8 +185,22 @@ __device__ __forceinline__ double rsqrt_nr(double x) { return 1.0 / sqrt(x); }
 //   zeta = (beta - alpha) / (2|g|),  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1/sqrt(1 + t^2),  s e^{i phi} = c t g/|g|;
 // the squared norms become alpha - t|g| and beta + t|g|.  Returns false when the
-// pair is already orthogonal to tol |x| |y| (or a row vanishes).  One division;
-// the reciprocal square roots are refined to about one ulp.
+// pair is already orthogonal to tol |x| |y| (or a row vanishes).  The reciprocal
+// square roots are refined to about one ulp.
+// t only selects the rotation angle: c and s follow from t through the refined
+// reciprocal square root, so the rotation is unitary to working precision
+// whatever rounding t carries.  Single precision therefore takes sqrt(1 + zeta^2)
+// and the quotient from the hardware estimates (a few ulp); double divides.
+__device__ __forceinline__ float tangent(float zeta, float az) {
+  const float y = fmaf(zeta, zeta, 1.0f);
+  const float root = az < 1e18f ? y * rsqrtf(y) : az;
+  return __fdividef(zeta >= 0.f ? 1.0f : -1.0f, az + root);
+}
+__device__ __forceinline__ double tangent(double zeta, double az) {
+  const double root = az < 1e18 ? sqrt(fma(zeta, zeta, 1.0)) : az;
+  return (zeta >= 0.0 ? 1.0 : -1.0) / (az + root);
+}
+
 template <typename R>
 __device__ __forceinline__ bool rot_params(R gx, R gy, R alpha, R beta, R tol, R& cs, R& sex,
                                            R& sey, R& tga) {
@@ -194,9 +208,7 @@ __device__ __forceinline__ bool rot_params(R gx, R gy, R alpha, R beta, R tol, R
   if (!(alpha > (R)0 && beta > (R)0 && g2 > tol * tol * alpha * beta)) return false;
   const R inv = rsqrt_nr(g2);
   const R zeta = (beta - alpha) * (R)0.5 * inv;
-  const R az = fabs(zeta);
-  const R root = az < (R)1e18 ? sqrt(fma(zeta, zeta, (R)1)) : az;
-  const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (az + root);
+  const R t = tangent(zeta, fabs(zeta));
   cs = rsqrt_nr(fma(t, t, (R)1));
   const R sn = cs * t;
   sex = sn * gx * inv;
@@ -340,6 +352,7 @@ struct BJRows {
 template <int CPL, int P0, int Q0, int P1, int Q1, int P2, int Q2, int P3, int Q3>
 __device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any, int& nrot) {
   const int lane = threadIdx.x & 31;
+  const float2 ONE2 = make_float2(1.f, 1.f), MONE2 = make_float2(-1.f, -1.f);
   float v[8];
 #define LT_BJ_DOT(K, P, Q)                                                   \
   {                                                                         \
@@ -350,8 +363,9 @@ __device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any,
       C = pfma(w.i[P][j], w.r[Q][j], C);                                    \
       D = pfma(w.r[P][j], w.i[Q][j], D);                                    \
     }                                                                       \
-    v[2 * K] = (A.x + A.y) + (B.x + B.y);                                   \
-    v[2 * K + 1] = (C.x + C.y) - (D.x + D.y);                               \
+    const float2 AB = pfma(B, ONE2, A), CD = pfma(D, MONE2, C);             \
+    v[2 * K] = AB.x + AB.y;                                                 \
+    v[2 * K + 1] = CD.x + CD.y;                                             \
   }
   LT_BJ_DOT(0, P0, Q0)
   LT_BJ_DOT(1, P1, Q1)
@@ -817,12 +831,20 @@ __device__ __forceinline__ void lq_build(const LQRow<G>& x, float* ebr, float* e
   if (q == 0) {
     const int p = (jn % G) * PART + jn / G;
     const float x0r = ebr[p], x0i = ebi[p];
-    const float alpha = sqrtf(a2), ax0 = sqrtf(x0r * x0r + x0i * x0i);
+    // square roots from the refined reciprocal square root (about one ulp)
+    const float n0 = x0r * x0r + x0i * x0i;
+    const float alpha = a2 > 0.f ? a2 * rsqrt_nr(a2) : 0.f;
     const bool tiny = !(alpha > TinyNorm<float>::v);
-    const float phr = ax0 > 0.f ? x0r / ax0 : 1.f, phi = ax0 > 0.f ? x0i / ax0 : 0.f;
+    float phr = 1.f, phi = 0.f, ax0 = 0.f;
+    if (n0 > 0.f) {
+      const float inv0 = rsqrt_nr(n0);
+      phr = x0r * inv0;
+      phi = x0i * inv0;
+      ax0 = n0 * inv0;
+    }
     ebr[p] = x0r + phr * alpha;
     ebi[p] = x0i + phi * alpha;
-    *bt_out = tiny ? 0.f : 2.f / (2.f * alpha * (alpha + ax0));
+    *bt_out = tiny ? 0.f : __frcp_rn(alpha * (alpha + ax0));
     diag[jn] = tiny ? make_float2(0.f, 0.f) : make_float2(-phr * alpha, -phi * alpha);
   }
   __syncwarp(pm);
