@@ -312,7 +312,9 @@ def run_ours(args):
 
     # ---- plain FP64 path on a subset (same kernels in double precision) ----------------
     fp64 = None
-    if args.fp64_traj > 0 and rank == 0:
+    # single-GPU legs run at N = 1 only (in a scaling run they would hold every GPU)
+    solo = world == 1
+    if args.fp64_traj > 0 and solo:
         n64 = args.fp64_traj
         e64 = lt.Ensemble(L, chi, n64, precision=lt.LT_FP64, init="neel",
                           stream=stream.cuda_stream, **w3_kwargs("fp64"))
@@ -332,7 +334,7 @@ def run_ours(args):
 
     # ---- quantum state diffusion leg (Sec. 5.2), one GPU -------------------------------
     qsd = None
-    if args.qsd_traj > 0 and rank == 0:
+    if args.qsd_traj > 0 and solo:
         Lq, nq, dtq = 128, args.qsd_traj, 0.01
         mq, pq = state_pool(Lq, chi, POOL, seed=4321)
         eq = lt.Ensemble(Lq, chi, nq, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
@@ -362,7 +364,7 @@ def run_ours(args):
 
     # ---- serving: Poisson arrivals of mixed requests through the request server --------
     serving = None
-    if args.serve_requests > 0 and rank == 0:
+    if args.serve_requests > 0 and solo:
         rng = np.random.default_rng(77)
         n_req, rate = args.serve_requests, args.serve_rate
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
@@ -412,7 +414,7 @@ def run_ours(args):
 
     # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
     accuracy = None
-    if args.acc_traj > 0 and rank == 0:
+    if args.acc_traj > 0 and solo:
         na = args.acc_traj
         ea = lt.Ensemble(L, chi, na, precision=lt.LT_FP64, init="neel",
                          stream=stream.cuda_stream, **w3_kwargs("fp64"))
@@ -482,7 +484,7 @@ def run_ours(args):
                            % args.steps}
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if solo and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_seconds)
 
     if rank == 0:
