@@ -63,7 +63,7 @@ typedef enum {
 
 typedef struct {
   int32_t L;                 /* chain length, 2 <= L <= 1024                       */
-  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 64             */
+  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 128            */
   int32_t n_traj;            /* trajectories held by this context, >= 1            */
   int32_t kraus_dim;         /* unused by LT_TRAJ (purified method), set 0         */
   int32_t method;            /* lt_method; LT_TRAJ and LT_QSD are built            */

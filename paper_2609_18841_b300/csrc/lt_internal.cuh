@@ -9,8 +9,14 @@
 
 #include "lindtebd.h"
 
-#define LT_MAX_CHI 64
+#define LT_MAX_CHI 128
 #define LT_MAX_DIM (2 * LT_MAX_CHI)  // largest theta side, d * chi_max
+// the single-precision register paths of the two-site update (row-resident
+// Householder steps, blocked Jacobi, V_k^+ assembly) cover theta sides up to
+// LT_REG_DIM and up to LT_REG_CHI kept values; larger tasks take the
+// shared/global-memory paths
+#define LT_REG_DIM 128
+#define LT_REG_CHI 64
 #define LT_BLOCK 256
 #define LT_NCOUNTERS 6
 
@@ -247,3 +253,5 @@ cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long 
 cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev);
 size_t bond_smem_bytes(int chi, size_t celt);
 size_t env_scratch_elems(int L, int chi);
+#define LT_ENV_SCRATCH_BYTES (4ull << 30)  // cap of the environment kernels' scratch
+long long env_grid_cap(int L, int chi, size_t celt, int num_sms);

@@ -1154,7 +1154,7 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
 
 template <typename R>
 __device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
-  blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64;
+  blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64 && nJ <= LT_REG_DIM;
   npad = blocked ? (nJ <= 64 ? 64 : 128)
                  : 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(nJ);
   mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
@@ -1243,12 +1243,18 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     bool blk2;
     int npad2, mp2;
     jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
-    if constexpr (sizeof(R) == 4)
-      qr_precondition_reg<BondShape<R>::NT / LT_MAX_DIM>(
-          reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ, rr, mp2, npad2,
-          reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta));
-    else
+    // register paths for the sizes they hold (every task up to chi_max = 64)
+    const bool reg = sizeof(R) == 4 && mJ <= LT_REG_DIM && nJ <= LT_REG_DIM && kmax <= LT_REG_CHI;
+    if constexpr (sizeof(R) == 4) {
+      if (reg)
+        qr_precondition_reg<BondShape<R>::NT / LT_REG_DIM>(
+            reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ, rr, mp2, npad2,
+            reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta));
+      else
+        qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
+    } else {
       qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
+    }
     int sweeps;
     if (blk2) {
       if (npad2 == 64)
@@ -1345,12 +1351,17 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     __syncthreads();
     const int k = s_k;
     // V_k^+ rows: row perm j holds sigma_j w_j^+; v_j^+ = w_j^+ Q1^+ goes to Y[j]
-    if constexpr (sizeof(R) == 4)
-      apply_q1_reg<BondShape<R>::NT / LT_MAX_CHI>(reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi), ldp, nJ,
-                   rr, k, s_perm, s_sig, reinterpret_cast<const float2*>(Y),
-                   reinterpret_cast<const float*>(s_beta), reinterpret_cast<float2*>(Y), ld);
-    else
+    if constexpr (sizeof(R) == 4) {
+      if (reg)
+        apply_q1_reg<BondShape<R>::NT / LT_REG_CHI>(
+            reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi), ldp, nJ, rr, k,
+            s_perm, s_sig, reinterpret_cast<const float2*>(Y), reinterpret_cast<const float*>(s_beta),
+            reinterpret_cast<float2*>(Y), ld);
+      else
+        apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
+    } else {
       apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
+    }
     __syncthreads();
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
@@ -2016,11 +2027,11 @@ size_t bond_smem_bytes(int chi, size_t celt) {
   auto npad_of = [&](size_t m, size_t n) {
     size_t gs = 1;
     while (gs * 2 * epp < n && gs < 32) gs <<= 1;
-    const bool blk = single && m >= 32 && n >= 64;
+    const bool blk = single && m >= 32 && n >= 64 && n <= LT_REG_DIM;
     return blk ? (n <= 64 ? (size_t)64 : (size_t)128) : 2 * epp * gs;
   };
   auto mp_of = [&](size_t m, size_t n) {
-    return (single && m >= 32 && n >= 64) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
+    return (single && m >= 32 && n >= 64 && n <= LT_REG_DIM) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
   };
   const size_t c2 = 2 * (size_t)chi, c1 = chi;
   // mode 0: theta 2chi x 2chi, V^+ chi x (2chi+1), B_{b+1} staged in V^+'s region
@@ -2037,6 +2048,15 @@ size_t bond_smem_bytes(int chi, size_t celt) {
 }
 
 size_t env_scratch_elems(int L, int chi) { return ((size_t)L + 1 + 7) * (size_t)chi * chi; }
+
+// CTAs of the environment kernels: each holds (L + 8) chi^2 elements of scratch,
+// so their number is capped to keep it within LT_ENV_SCRATCH_BYTES (one CTA per SM
+// at least)
+long long env_grid_cap(int L, int chi, size_t celt, int num_sms) {
+  const long long per = (long long)(env_scratch_elems(L, chi) * celt);
+  const long long cap = (long long)LT_ENV_SCRATCH_BYTES / (per > 0 ? per : 1);
+  return cap > num_sms ? cap : num_sms;
+}
 
 template <typename R>
 static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0,
@@ -2315,7 +2335,9 @@ int env_grid(lt_ctx_s* c) {
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_tiled_kernel<double>, LT_BLOCK, 0);
   if (e != cudaSuccess || occ < 1) occ = 2;
   if (occ > 8) occ = 8;
-  const long long g = (long long)occ * c->num_sms;
+  long long g = (long long)occ * c->num_sms;
+  const long long cap = env_grid_cap(c->L, c->chi, c->celt, c->num_sms);
+  if (g > cap) g = cap;
   return (int)(g < c->n_traj ? g : c->n_traj);
 }
 

@@ -72,7 +72,9 @@ uint64_t context_bytes(const lt_config* cfg, int num_sms) {
   b += (2 * L * L + 2 * L) * 8;                            // reduction buffer
   const uint64_t need = bond_smem_bytes((int)chi, celt);
   if (need > 200 * 1024) b += 2ull * num_sms * need;       // bond scratch when not in shared memory
-  const uint64_t env_grid = nt < 8ull * num_sms ? nt : 8ull * num_sms;
+  uint64_t env_grid = nt < 8ull * num_sms ? nt : 8ull * num_sms;
+  const uint64_t cap = (uint64_t)env_grid_cap((int)L, (int)chi, celt, num_sms);
+  if (env_grid > cap) env_grid = cap;
   b += env_grid * env_scratch_elems((int)L, (int)chi) * celt;
   return b;
 }

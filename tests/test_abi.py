@@ -34,7 +34,7 @@ def test_config_struct_layout_matches_header():
 
 
 @pytest.mark.parametrize("kw,status", [
-    (dict(L=1), 1), (dict(chi_max=0), 1), (dict(chi_max=65), 1), (dict(n_traj=0), 1),
+    (dict(L=1), 1), (dict(chi_max=0), 1), (dict(chi_max=129), 1), (dict(n_traj=0), 1),
     (dict(dt=0.0), 1), (dict(trotter_order=3), 1), (dict(precision=5), 1),
     (dict(method=1, gamma_loss=0.1), 7), (dict(method=2), 7), (dict(gamma_loss=-0.1), 1),
     (dict(init="product"), 1),

@@ -113,7 +113,8 @@ def test_w1_mixed_replay_error_bounds(w1_oracle):
 
 # ---- synthetic states: ragged dims, several tiles, truncation active ---------------------
 @pytest.mark.parametrize("L,chi,ragged,seed", [(10, 8, True, 1), (12, 16, True, 2),
-                                               (9, 5, False, 3), (16, 32, True, 4)])
+                                               (9, 5, False, 3), (16, 32, True, 4),
+                                               (16, 128, False, 5)])
 def test_synthetic_state_one_step_fp64(L, chi, ragged, seed):
     w = dict(workloads.W3, L=L, chi_max=chi, gamma_loss=0.3, gamma_gain=0.05, gamma_deph=0.1)
     cfg = oracle_cfg(w, L=L, chi=chi, dt=0.05, seed=seed)
@@ -310,3 +311,20 @@ def test_contexts_of_different_chi_live_side_by_side():
     with gpu_ensemble(cfg_small, 2, lt.LT_MIXED) as ref:
         gpu_steps(ref, cfg_small, 4)
         assert np.array_equal(ref.density(per_traj=True)[2], d_small)
+
+
+
+def test_chi128_mixed_two_steps():
+    """chi_max = 128 (theta up to 256 x 256, beyond the register paths) in mixed
+    precision, jump records replayed from the oracle."""
+    L, chi, n = 16, 128, 2
+    w = dict(workloads.W3, L=L, chi_max=chi, gamma_loss=0.3, gamma_deph=0.1)
+    cfg = oracle_cfg(w, L=L, chi=chi, dt=0.05, seed=6)
+    states = [workloads.synthetic_mps(L, chi, seed=700 + t) for t in range(n)]
+    res = tebd.run_trajectories(cfg, 2, list(range(n)), initial=[(B, lam) for B, lam, _ in states])
+    lt = _lt()
+    with gpu_ensemble(cfg, n, lt.LT_MIXED) as ens:
+        ens.set_state(0, states)
+        gpu_steps(ens, cfg, 2, replay=res["jumps"])
+        _, _, dens = ens.density(per_traj=True)
+    assert_close(dens, res["density"], 2e-5, "chi 128 mixed density")
