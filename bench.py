@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--acc-traj", type=int, default=32)
     ap.add_argument("--qsd-traj", type=int, default=1024)
     ap.add_argument("--qsd-steps", type=int, default=2)
+    ap.add_argument("--qsd-chi128-traj", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
@@ -367,6 +368,27 @@ def run_ours(args):
                "ms_per_step": 1e3 * sq / args.qsd_steps, "steps": args.qsd_steps,
                "log_weight_range": [float(lw.min()), float(lw.max())]}
         eq.close()
+        # the configuration's own chi_max = 128 (theta up to 256 x 256), fewer histories
+        if args.qsd_chi128_traj > 0:
+            n8 = args.qsd_chi128_traj
+            m8, p8 = state_pool(Lq, 128, 8, seed=4321)
+            e8 = lt.Ensemble(Lq, 128, n8, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
+                             dt=dtq, gamma_loss=0.05, gamma_deph=0.1, fermionic_jumps=0,
+                             svd_cut=1e-6, stream=stream.cuda_stream)
+            upload(lt, e8.ctx, p8, n8)
+            torch.cuda.synchronize()
+            e8.counters(clear=True)
+            a.record(stream)
+            lt.lt_step(e8.ctx, 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            c8 = e8.counters()
+            s8 = a.elapsed_time(b) / 1e3
+            qsd["chi128"] = {"histories": n8, "steps": 1, "ms_per_step": 1e3 * s8,
+                             "updates_per_s": c8["updates"] / s8,
+                             "layer_updates_per_s": c8["layer_updates"] / s8}
+            e8.close()
+            del m8, p8
 
     # ---- serving: Poisson arrivals of mixed requests through the request server --------
     serving = None
