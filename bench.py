@@ -399,8 +399,8 @@ def run_ours(args):
         reqs = []
         for i in range(n_req):
             qsd_req = bool(rng.integers(2))
-            kw = dict(n_steps=int(rng.integers(10, 31)), L=int(rng.choice([16, 32, 64])),
-                      chi_max=int(rng.choice([16, 32, 64])), n_traj=int(rng.choice([1, 8, 32, 128])),
+            kw = dict(n_steps=int(rng.integers(10, 31)), L=int(rng.choice([16, 32, 64, 128])),
+                      chi_max=int(rng.choice([32, 64, 128])), n_traj=int(rng.choice([1, 8, 32, 128])),
                       precision=lt.LT_MIXED, method=lt.LT_QSD if qsd_req else lt.LT_TRAJ,
                       dt=0.02, seed=100 + i, svd_cut=1e-6, init="neel")
             if qsd_req:
@@ -435,9 +435,10 @@ def run_ours(args):
                    "completed_per_s": len(lat) / wall,
                    "latency_s": {"p50": float(np.percentile(lat, 50)),
                                  "p99": float(np.percentile(lat, 99))} if lat else None,
-                   "mix": "trajectory or QSD (1:1), L in {16,32,64}, chi_max in {16,32,64}, "
-                          "1..128 trajectories, 10..30 steps of dt=0.02, mixed precision, "
-                          "Neel start; Poisson arrivals; latency from submission to completion",
+                   "mix": "trajectory or QSD (1:1), L in {16,32,64,128}, chi_max in "
+                          "{32,64,128}, 1..128 trajectories, 10..30 steps of dt=0.02, mixed "
+                          "precision, Neel start; Poisson arrivals; latency from submission to "
+                          "completion",
                    "budget_gb": args.serve_budget_gb}
 
     # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
