@@ -138,3 +138,26 @@ def test_qsd_step_checkpoint_and_method_errors(tmp_path):
     with pytest.raises(lt.LtError) as e:
         lt.Ensemble(8, 8, 2, method=lt.LT_QSD, gamma_loss=0.1, fermionic_jumps=1)
     assert e.value.status == lt.LT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("L,chi,fermionic,loss,gain,deph", [
+    (2, 1, True, [0.3, 0.0], 0.0, 0.2),          # one bond, product states only
+    (6, 8, False, 0.1, 0.2, 0.1),                # spin gain and loss on every site
+    (7, 4, True, [0.4] + [0.0] * 6, 0.0, 0.15),  # odd length, truncation at chi 4
+])
+def test_qsd_gain_edges_and_small_chains(L, chi, fermionic, loss, gain, deph):
+    cfg = tebd.TrajectoryConfig(L, J=1.0, dt=0.05, chi_max=chi, svd_cut=1e-12, gamma_loss=loss,
+                                gamma_gain=gain, gamma_deph=deph, fermionic=fermionic,
+                                occupation=workloads.occupation(L, "neel"), seed=9)
+    n, steps = 3, 6
+    res = tebd.run_qsd(cfg, steps, list(range(n)))
+    lt = _lt()
+    with lt.Ensemble(L, chi, n, method=lt.LT_QSD, precision=lt.LT_FP64, init="neel", J=1.0,
+                     dt=0.05, gamma_loss=cfg.gamma_loss, gamma_gain=cfg.gamma_gain,
+                     gamma_deph=cfg.gamma_deph, fermionic_jumps=int(fermionic), svd_cut=1e-12,
+                     seed=9) as ens:
+        ens.step(steps)
+        _, _, dens = ens.density(per_traj=True)
+        logw = ens.log_weights()
+    close(logw, res["log_weight"], FP64_TOL, "log weight")
+    close(dens, res["density"], FP64_TOL, "density")
