@@ -13,6 +13,9 @@ Modules
            EffHamiltonian; Sec. 2.3 Trotter splitting).
   tebd     the MPS quantum-trajectory integrator in Vidal-Hastings form
            (Sec. 2.3 Eq. Theta, Sec. 4.1 Eqs. QJump1, TransitionRate).
+  mpdo     the vectorised density matrix (MPDO, d^2 = 4) under Liouvillian
+           TEBD gates (Sec. 3.1, Eqs. Choi, LindbladChoi, Liouvillian, MPDO),
+           with traces Tr(O rho) / Tr rho for the observables.
   dense    brute-force references: the dense Trotterised state vector, dense
            Lindblad integration of rho, and the correlation-matrix equation of
            motion (Sec. 2.1 Eqs. eqCorr, SoleqCorr; Eq. Lindblad).
