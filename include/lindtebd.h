@@ -8,7 +8,12 @@
  * update of Sec. 2.3 (Eq. Theta): contract Lambda_{b-1} B_b B_{b+1} with the
  * two-site gate exp(-i h_b^eff tau) into theta, take a truncated SVD back to
  * chi_max and renormalise (Sec. 2.3, Eq. TruncationErr and the normalisation
- * that follows it).
+ * that follows it).  The same update serves quantum state diffusion (Sec. 5.2,
+ * method LT_QSD) and the vectorised density matrix (Sec. 3.1, method LT_MPDO):
+ * |rho>> = sum_ij rho_ij |i> (x) |j> (Eq. Choi) as an MPS with the local index
+ * m = 2n + n' of four values (Eq. MPDO), advanced by the two-site Liouvillian
+ * gates exp(tau Lv_b) (Eq. Liouvillian).  An LT_MPDO context holds n_traj
+ * independent chains (one density matrix each; they share the rates).
  *
  * Conventions shared by every entry point
  *  - Sites 0..L-1, bond b joins sites b and b+1, single-site basis |0> empty,
@@ -63,10 +68,11 @@ typedef enum {
 
 typedef struct {
   int32_t L;                 /* chain length, 2 <= L <= 1024                       */
-  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 128            */
+  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 128 (<= 64 for */
+                             /* LT_MPDO, whose theta is 4 chi wide)                */
   int32_t n_traj;            /* trajectories held by this context, >= 1            */
   int32_t kraus_dim;         /* unused by LT_TRAJ (purified method), set 0         */
-  int32_t method;            /* lt_method; LT_TRAJ and LT_QSD are built            */
+  int32_t method;            /* lt_method; LT_TRAJ, LT_QSD and LT_MPDO are built   */
   int32_t precision;         /* lt_precision                                       */
   int32_t init;              /* lt_init                                            */
   int32_t trotter_order;     /* 1: A(dt) B(dt); 2: A(dt/2) B(dt) A(dt/2)           */
@@ -87,7 +93,13 @@ typedef struct {
 
 /* Create a context: validate cfg, allocate the ensemble on the current device
  * and set every trajectory to the initial product state (Sec. 4.1: the
- * initial pure state is an eigenvector of rho(0), here a product state).
+ * initial pure state is an eigenvector of rho(0), here a product state); an
+ * LT_MPDO chain starts from rho = |n><n| of that product state (local index
+ * 3 n_i on every site).  LT_ERR_UNSUPPORTED: LT_PURIFIED; LT_MPDO with
+ * chi_max > 64, or with fermionic loss or gain on a bulk site (on the chain
+ * ends the Jordan-Wigner string acts as the total parity, which commutes with
+ * every state reached from a product state, so c and c^+ act there as the
+ * local sigma- and sigma+; in the bulk they would not be local).
  * stream: a cudaStream_t, or NULL for a stream the context creates and owns.
  * On success *out holds the context; on failure *out is NULL. */
 lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out);
@@ -101,7 +113,13 @@ lt_status lt_destroy(lt_ctx ctx);
  * the first call).  h_b^eff carries half of each bulk site's dissipator
  * -(i/2) sum_k gamma_k L_k^+ L_k and the whole of an end site's (Eq.
  * EffHamiltonian, split as in Eq. LindbladLocal).  Gates are built on the host
- * in double precision once per distinct tau. */
+ * in double precision once per distinct tau.  In an LT_MPDO context the gate
+ * is the 16 x 16 matrix exp(tau Lv_b) over (m_b, m_{b+1}) with
+ * Lv_b = -i(h_b (x) 1 - 1 (x) h_b^T) + the same weighted site dissipators
+ * sum_k gamma_k [L_k (x) conj(L_k) - 1/2 L_k^+L_k (x) 1 - 1/2 1 (x) (L_k^+L_k)^T]
+ * (Eq. Liouvillian, with the conjugate and transpose that the vectorisation
+ * gives), and the update renormalises the Hilbert-Schmidt norm of |rho>>, so
+ * its scale is arbitrary and every observable is a ratio to Tr rho. */
 lt_status lt_apply_layer(lt_ctx ctx, int32_t parity, double tau);
 
 /* Jump-or-evolve decision of time step `step` (Sec. 4.1): for every
@@ -143,7 +161,8 @@ lt_status lt_get_log_weights(lt_ctx ctx, double* out);
 /* n_steps full time steps with step counting on from the context's step
  * counter (starting at 0): for LT_TRAJ lt_apply_jumps(step, NULL, NULL) then
  * the layers of the configured Trotter order; for LT_QSD the layers then
- * lt_apply_noise(step). */
+ * lt_apply_noise(step); for LT_MPDO the layers only (lt_apply_jumps and
+ * lt_apply_noise return LT_ERR_UNSUPPORTED there). */
 lt_status lt_step(lt_ctx ctx, int32_t n_steps);
 
 /* Ensemble density <n_i> = <psi|n_i|psi>/<psi|psi> (exact environments).
@@ -151,13 +170,17 @@ lt_status lt_step(lt_ctx ctx, int32_t n_steps);
  * (Eq. ErrorCLT), or NULL; per_traj: [n_traj * L] row-major, or NULL.  For
  * LT_QSD the ensemble quantities average w_t <n_i>_t with w_t = <psi_t|psi_t>
  * (the mean of |psi><psi| over unnormalised histories, Sec. 5.2), while
- * per_traj holds the normalised <n_i>_t. */
+ * per_traj holds the normalised <n_i>_t.  For LT_MPDO per_traj holds each
+ * chain's Re Tr(n_i rho) / Tr rho, the traces contracting |rho>> with the
+ * vectors o[2n + n'] = O[n', n] of each site's operator, and mean/sem run over
+ * the chains. */
 lt_status lt_measure_density(lt_ctx ctx, double* mean, double* sem, double* per_traj);
 
 /* Correlation matrix C_ij = <c_i^+ c_j> (Sec. 2.1) by transfer matrices with
  * the Jordan-Wigner string.  C_re/C_im: [L * L] row-major ensemble mean
  * (weighted as for the density in LT_QSD contexts); per_traj_re/per_traj_im:
- * [n_traj * L * L] normalised, or NULL. */
+ * [n_traj * L * L] normalised, or NULL.  For LT_MPDO C_ij = Tr(c_i^+ c_j rho) /
+ * Tr rho for i < j, C_ji = conj(C_ij), C_ii = <n_i>. */
 lt_status lt_measure_corr(lt_ctx ctx, double* C_re, double* C_im,
                           double* per_traj_re, double* per_traj_im);
 
@@ -167,9 +190,10 @@ lt_status lt_get_stats(lt_ctx ctx, double* trunc_weight, int32_t* bond_dims);
 
 /* Replace / read trajectories traj0 .. traj0+n-1.  Layout per trajectory:
  * dims [L-1] int32; lam [(L-1) * chi_max] double, bond b at b * chi_max;
- * B [L * 2 * chi_max^2] complex128 as interleaved (re, im) doubles, site i at
- * i * 2 * chi_max^2, holding B_i[a][s][c] row-major over its actual shape
- * (chi_{i-1}, 2, chi_i).  Dimensions must satisfy 1 <= chi_b <= chi_max.
+ * B [L * d * chi_max^2] complex128 as interleaved (re, im) doubles, site i at
+ * i * d * chi_max^2, holding B_i[a][s][c] row-major over its actual shape
+ * (chi_{i-1}, d, chi_i), d = 2 (d = 4 for LT_MPDO, s the local index
+ * m = 2n + n').  Dimensions must satisfy 1 <= chi_b <= chi_max.
  * lt_set_state also clears the truncation accumulators and the log weights of
  * those trajectories. */
 lt_status lt_set_state(lt_ctx ctx, int32_t traj0, int32_t n, const int32_t* dims,
@@ -206,7 +230,7 @@ lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear)
 lt_status lt_get_counters(lt_ctx ctx, uint64_t* out, int32_t clear);
 
 /* ---- request server (continuous batching; the paper has no serving layer) ----
- * A request is one ensemble (an lt_config, method LT_TRAJ or LT_QSD) run for
+ * A request is one ensemble (an lt_config, method LT_TRAJ, LT_QSD or LT_MPDO) run for
  * n_steps time steps.  Each admitted request owns a context and its stream on
  * the current device, so the steps of all active requests are queued side by
  * side and the GPU interleaves their kernels; the ensemble stays resident from

@@ -102,17 +102,160 @@ void build_gates(const lt_ctx_s* c, double tau, std::vector<double2>& out) {
   }
 }
 
+// ---- Liouvillian gates of the vectorised density matrix (Sec. 3.1) -----------------------
+// |rho>> = sum_ij rho_ij |i> (x) |j> (Eq. Choi) turns rho -> A rho B into a matrix;
+// on one bond, over the local indices m = 2n + n' of its two sites (Eq. MPDO),
+// its entry [(m_b, m_{b+1}), (k_b, k_{b+1})] is A[(n_b n_{b+1}), (k_b k_{b+1})]
+// B[(k'_b k'_{b+1}), (n'_b n'_{b+1})].  The bond generator is
+//   Lv_b = -i [h_b, .] + w_l D_b + w_r D_{b+1},
+//   D_i rho = sum_k gamma_k (L_k rho L_k^+ - 1/2 L_k^+L_k rho - 1/2 rho L_k^+L_k),
+// which in (x) form carries L (x) conj(L) and 1 (x) h^T (Eq. Liouvillian read
+// with the conjugate and transpose the map produces).  Loss sigma-, gain sigma+,
+// dephasing n; the weights split the site terms as for the trajectory gates.
+// A fermionic loss or gain is accepted on the chain ends only, where its string
+// acts as the total parity, which commutes with every state reached from a
+// product state, so the local operator gives the same evolution.
+typedef std::vector<cd> Mat;
+
+Mat mat_mul(const Mat& a, const Mat& b, int n) {
+  Mat r((size_t)n * n, cd(0.0, 0.0));
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const cd x = a[(size_t)i * n + k];
+      if (x == cd(0.0, 0.0)) continue;
+      for (int j = 0; j < n; ++j) r[(size_t)i * n + j] += x * b[(size_t)k * n + j];
+    }
+  return r;
+}
+
+// exp(A) for an n x n matrix, the same scaling-and-squaring Taylor rule as expm4
+Mat expm_n(Mat A, int n) {
+  double nrm = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double col = 0.0;
+    for (int i = 0; i < n; ++i) col += std::abs(A[(size_t)i * n + j]);
+    nrm = col > nrm ? col : nrm;
+  }
+  int s = 0;
+  while (nrm > 0.5) {
+    nrm *= 0.5;
+    ++s;
+  }
+  const double scale = std::ldexp(1.0, -s);
+  for (auto& x : A) x *= scale;
+  Mat E((size_t)n * n, cd(0.0, 0.0)), term;
+  for (int i = 0; i < n; ++i) E[(size_t)i * n + i] = 1.0;
+  term = E;
+  for (int k = 1; k < 40; ++k) {
+    term = mat_mul(term, A, n);
+    double mx = 0.0;
+    for (auto& x : term) {
+      x /= (double)k;
+      mx = std::abs(x) > mx ? std::abs(x) : mx;
+    }
+    for (size_t i = 0; i < E.size(); ++i) E[i] += term[i];
+    if (mx < 1e-18) break;
+  }
+  for (int k = 0; k < s; ++k) E = mat_mul(E, E, n);
+  return E;
+}
+
+// S += coef * (rho -> A rho B) on the 16-dimensional two-site space
+void add_superop(Mat& S, const M4& A, const M4& B, cd coef) {
+  for (int nb = 0; nb < 2; ++nb)
+    for (int pb = 0; pb < 2; ++pb)
+      for (int nc = 0; nc < 2; ++nc)
+        for (int pc = 0; pc < 2; ++pc) {
+          const int row = (2 * nb + pb) * 4 + (2 * nc + pc);
+          for (int kb = 0; kb < 2; ++kb)
+            for (int qb = 0; qb < 2; ++qb)
+              for (int kc = 0; kc < 2; ++kc)
+                for (int qc = 0; qc < 2; ++qc) {
+                  const int col = (2 * kb + qb) * 4 + (2 * kc + qc);
+                  S[(size_t)row * 16 + col] += coef * A.v[(nb * 2 + nc) * 4 + (kb * 2 + kc)] *
+                                               B.v[(qb * 2 + qc) * 4 + (pb * 2 + pc)];
+                }
+        }
+}
+
+// one-site 2x2 operator on the left (side 0) or right (side 1) site of a bond
+M4 on_site(const cd op[4], int side) {
+  M4 r;
+  for (auto& x : r.v) x = 0;
+  for (int sb = 0; sb < 2; ++sb)
+    for (int sc = 0; sc < 2; ++sc)
+      for (int tb = 0; tb < 2; ++tb)
+        for (int tc = 0; tc < 2; ++tc) {
+          cd v = side == 0 ? (sc == tc ? op[sb * 2 + tb] : cd(0.0, 0.0))
+                           : (sb == tb ? op[sc * 2 + tc] : cd(0.0, 0.0));
+          r.v[(sb * 2 + sc) * 4 + (tb * 2 + tc)] = v;
+        }
+  return r;
+}
+
+M4 adjoint(const M4& a) {
+  M4 r;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) r.v[i * 4 + j] = std::conj(a.v[j * 4 + i]);
+  return r;
+}
+
+void build_liouvillian_gates(const lt_ctx_s* c, double tau, std::vector<double2>& out) {
+  const int L = c->L;
+  out.assign((size_t)(L - 1) * 256, make_double2(0, 0));
+  M4 one, h;
+  for (int i = 0; i < 16; ++i) {
+    one.v[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    h.v[i] = 0.0;
+  }
+  h.v[2 * 4 + 1] = -c->J;  // |10><01|
+  h.v[1 * 4 + 2] = -c->J;  // |01><10|
+  M4 mih, pih;
+  for (int i = 0; i < 16; ++i) {
+    mih.v[i] = cd(0.0, -1.0) * h.v[i];
+    pih.v[i] = cd(0.0, 1.0) * h.v[i];
+  }
+  const cd sminus[4] = {0.0, 1.0, 0.0, 0.0}, splus[4] = {0.0, 0.0, 1.0, 0.0},
+           number[4] = {0.0, 0.0, 0.0, 1.0};
+  for (int b = 0; b < L - 1; ++b) {
+    Mat S(256, cd(0.0, 0.0));
+    add_superop(S, mih, one, 1.0);  // -i h rho
+    add_superop(S, one, pih, 1.0);  // +i rho h
+    const double w[2] = {b == 0 ? 1.0 : 0.5, b + 1 == L - 1 ? 1.0 : 0.5};
+    for (int side = 0; side < 2; ++side) {
+      const int site = b + side;
+      const double g[3] = {c->gl[site], c->gg[site], c->gd[site]};
+      const cd* ops[3] = {sminus, splus, number};
+      for (int k = 0; k < 3; ++k) {
+        if (!(g[k] > 0.0)) continue;
+        const M4 Lk = on_site(ops[k], side), Ld = adjoint(Lk);
+        const M4 LdL = mmul(Ld, Lk);
+        const double wg = w[side] * g[k];
+        add_superop(S, Lk, Ld, wg);
+        add_superop(S, LdL, one, -0.5 * wg);
+        add_superop(S, one, LdL, -0.5 * wg);
+      }
+    }
+    for (auto& x : S) x *= tau;
+    const Mat G = expm_n(S, 16);
+    for (int i = 0; i < 256; ++i)
+      out[(size_t)b * 256 + i] = make_double2(G[i].real(), G[i].imag());
+  }
+}
+
 lt_status gate_ptr(lt_ctx_s* c, double tau, const double2** out) {
+  const size_t per = (size_t)(c->L - 1) * c->d * c->d * c->d * c->d;
   for (size_t i = 0; i < c->gate_taus.size(); ++i)
     if (c->gate_taus[i] == tau) {
-      *out = c->gates + i * (size_t)(c->L - 1) * 16;
+      *out = c->gates + i * per;
       return LT_OK;
     }
   if (c->gate_taus.size() >= 8) return fail(c, LT_ERR_ARG, "lt_apply_layer", "more than 8 distinct tau values");
   std::vector<double2> h;
-  build_gates(c, tau, h);
+  if (c->d == 4) build_liouvillian_gates(c, tau, h);
+  else build_gates(c, tau, h);
   const size_t i = c->gate_taus.size();
-  double2* dst = c->gates + i * (size_t)(c->L - 1) * 16;
+  double2* dst = c->gates + i * per;
   LT_CK(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
   LT_CK(cudaStreamSynchronize(c->stream));
   c->gate_taus.push_back(tau);
@@ -216,7 +359,12 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (!out) return LT_ERR_ARG;
   *out = nullptr;
   if (!cfg) return LT_ERR_ARG;
-  if (cfg->method != LT_TRAJ && cfg->method != LT_QSD) return LT_ERR_UNSUPPORTED;
+  if (cfg->method != LT_TRAJ && cfg->method != LT_QSD && cfg->method != LT_MPDO)
+    return LT_ERR_UNSUPPORTED;
+  // theta of the vectorised density matrix is 4 chi x 4 chi: the two-site
+  // update holds sides up to LT_MAX_DIM
+  if (cfg->method == LT_MPDO && cfg->chi_max > LT_MAX_DIM / 4 && cfg->chi_max <= LT_MAX_CHI)
+    return LT_ERR_UNSUPPORTED;
   if (cfg->L < 2 || cfg->L > 1024 || cfg->chi_max < 1 || cfg->chi_max > LT_MAX_CHI ||
       cfg->n_traj < 1 || (cfg->precision != LT_FP64 && cfg->precision != LT_MIXED) ||
       (cfg->trotter_order != 1 && cfg->trotter_order != 2) || !(cfg->dt > 0.0) ||
@@ -260,6 +408,13 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
       delete c;
       return LT_ERR_UNSUPPORTED;
     }
+    // the vectorised density matrix takes c_i and c_i^+ as local operators on
+    // the chain ends only (there the string acts as the total parity)
+    if (c->method == LT_MPDO && c->fermionic && i > 0 && i < L - 1 &&
+        (c->gl[i] > 0.0 || c->gg[i] > 0.0)) {
+      delete c;
+      return LT_ERR_UNSUPPORTED;
+    }
   }
   c->occ.assign(L, 0);
   for (int i = 0; i < L; ++i) {
@@ -270,7 +425,8 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
       default: c->occ[i] = cfg->product_occ[i] ? 1 : 0;
     }
   }
-  c->slot = 2 * c->chi * c->chi;
+  c->d = c->method == LT_MPDO ? 4 : 2;
+  c->slot = c->d * c->chi * c->chi;
   c->celt = c->prec == LT_MIXED ? sizeof(float2) : sizeof(double2);
   lt_status st = LT_OK;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -293,7 +449,9 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   e = configure_bond(c);
   if (e != cudaSuccess) st = fail(c, LT_ERR_CUDA, "configure_bond", cudaGetErrorString(e));
   c->env_grid = env_grid(c);
-  c->env_scratch_stride = (long long)env_scratch_elems(L, c->chi);
+  c->env_scratch_stride = c->method == LT_MPDO
+                              ? (long long)(mpdo_scratch_bytes(L, c->chi) / c->celt)
+                              : (long long)env_scratch_elems(L, c->chi);
   if (st == LT_OK) st = dalloc(c, (char**)&c->B, nt * L * c->slot * c->celt);
   if (st == LT_OK) st = dalloc(c, &c->lam, nt * nb * c->chi);
   if (st == LT_OK) st = dalloc(c, &c->dims, nt * nb);
@@ -311,7 +469,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (st == LT_OK) st = dalloc(c, &c->err_dev, 1);
   if (st == LT_OK) st = dalloc(c, &c->sweep_hist, 64);
   if (st == LT_OK) st = dalloc(c, &c->counters, LT_NCOUNTERS);
-  if (st == LT_OK) st = dalloc(c, &c->gates, 8 * nb * 16);
+  if (st == LT_OK) st = dalloc(c, &c->gates, 8 * nb * (size_t)(c->d * c->d * c->d * c->d));
   if (st == LT_OK) st = dalloc(c, &c->red, 2 * (size_t)L * L + 2 * (size_t)L);
   if (st == LT_OK && !c->bond_use_smem)
     st = dalloc(c, (char**)&c->bond_scratch, (size_t)c->bond_grid * c->bond_scratch_stride * c->celt);
@@ -464,7 +622,8 @@ lt_status lt_step(lt_ctx c, int32_t n_steps) {
 lt_status lt_measure_density(lt_ctx c, double* mean, double* sem, double* per_traj) {
   lt_status st = guard(c);
   if (st != LT_OK) return st;
-  LT_CK(launch_env(c, 0, 0, nullptr));
+  if (c->method == LT_MPDO) LT_CK(launch_mpdo_trace(c, false));
+  else LT_CK(launch_env(c, 0, 0, nullptr));
   LT_CK(launch_reduce_density(c, c->red, c->red + c->L));
   if (mean) LT_CK(cudaMemcpyAsync(mean, c->red, sizeof(double) * c->L, cudaMemcpyDeviceToHost, c->stream));
   if (sem) LT_CK(cudaMemcpyAsync(sem, c->red + c->L, sizeof(double) * c->L, cudaMemcpyDeviceToHost, c->stream));
@@ -482,7 +641,8 @@ lt_status lt_measure_corr(lt_ctx c, double* C_re, double* C_im, double* per_re, 
     st = dalloc(c, &c->corr, LL * c->n_traj);
     if (st != LT_OK) return st;
   }
-  LT_CK(launch_corr(c));
+  if (c->method == LT_MPDO) LT_CK(launch_mpdo_trace(c, true));
+  else LT_CK(launch_corr(c));
   LT_CK(launch_reduce_corr(c, c->red));
   std::vector<double> m(2 * LL);
   LT_CK(cudaMemcpyAsync(m.data(), c->red, sizeof(double) * 2 * LL, cudaMemcpyDeviceToHost, c->stream));

@@ -180,9 +180,21 @@ struct EnvArgs {
   double2* corr;        // [n_traj][L][L] for the correlation kernel
 };
 
+// traces of the vectorised density matrix (method LT_MPDO)
+struct MpdoArgs {
+  const void* B;
+  const int* dims;
+  int L, chi, slot, n_traj;
+  double2* scratch;     // per-CTA [2][L + 1][chi] right and left vectors
+  long long stride;     // scratch elements (double2) per CTA
+  double* density;      // [n_traj][L]
+  double2* corr;        // [n_traj][L][L] or nullptr
+};
+
 // ---- context -------------------------------------------------------------------------
 struct lt_ctx_s {
   int L, chi, n_traj, prec, order, fermionic, max_sweeps, method;
+  int d;            // physical values per site: 2 (pure states), 4 (vectorised rho)
   double J, dt, cut, jacobi_tol;
   uint64_t seed;
   long long traj_offset;
@@ -195,7 +207,7 @@ struct lt_ctx_s {
   bool own_stream;
   int device, num_sms;
 
-  int slot;         // complex elements per site tensor slot = 2 chi^2
+  int slot;         // complex elements per site tensor slot = d chi^2
   size_t celt;      // bytes per complex element (8 mixed, 16 fp64)
   void* B;          // site tensors
   double* lam;
@@ -217,7 +229,7 @@ struct lt_ctx_s {
 
   // gate cache: up to 8 distinct tau values
   std::vector<double> gate_taus;
-  double2* gates;   // [8][L-1][16]
+  double2* gates;   // [8][L-1][d^4]
 
   void* bond_scratch;
   long long bond_scratch_stride;
@@ -246,12 +258,14 @@ cudaError_t launch_jump_apply(lt_ctx_s* c);
 cudaError_t launch_compact(lt_ctx_s* c);
 cudaError_t launch_qsd_noise(lt_ctx_s* c, long long step);
 cudaError_t launch_corr(lt_ctx_s* c);
+cudaError_t launch_mpdo_trace(lt_ctx_s* c, bool corr);
+size_t mpdo_scratch_bytes(int L, int chi);
 cudaError_t launch_reduce_density(lt_ctx_s* c, double* out_mean, double* out_sem);
 cudaError_t launch_reduce_corr(lt_ctx_s* c, double* out);
 cudaError_t launch_convert_in(lt_ctx_s* c, const double* src, long long n, long long dst_off);
 cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long src_off);
 cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev);
-size_t bond_smem_bytes(int chi, size_t celt);
+size_t bond_smem_bytes(int chi, size_t celt, int d);
 size_t env_scratch_elems(int L, int chi);
 #define LT_ENV_SCRATCH_BYTES (4ull << 30)  // cap of the environment kernels' scratch
 long long env_grid_cap(int L, int chi, size_t celt, int num_sms);

@@ -63,30 +63,33 @@ template <typename V, typename R> __device__ __forceinline__ V splat(R v) {
 }
 
 // ---- theta formation (Eq. Theta) -----------------------------------------------------
-// theta[(a,s'),(t',c)] = w_a sum_{s,t} G[s't',st] sum_mu Bl[a,s,mu] Br[mu,t,c], written
-// planar (real parts in Xr, imaginary parts in Xi, row stride ldp).  Br is first
-// staged in shared memory (Bs_in, chiM x 2chiR) when a staging area is given;
-// each thread computes two values of a for one column c, so consecutive lanes
-// read consecutive Bs words and share the broadcast Bl reads.  Columns n..npad-1
-// are set to zero (the Jacobi sweeps run over npad columns without tests), and
-// so are the padding rows 2 chiL .. mp-1.
-template <typename R>
+// theta[(a,s'),(t',c)] = w_a sum_{s,t} G[s't',st] sum_mu Bl[a,s,mu] Br[mu,t,c] with D
+// physical values per site (D = 2 for pure states; D = 4 for the vectorised
+// density matrix, m = 2n + n', Eq. MPDO), written planar (real parts in Xr,
+// imaginary parts in Xi, row stride ldp).  Br is first staged in shared memory
+// (Bs_in, chiM x D chiR) when a staging area is given.  For D = 2 each thread
+// computes two values of a for one column c, so consecutive lanes read
+// consecutive Bs words and share the broadcast Bl reads; for D = 4 a thread
+// takes one (a, c) and its 16 products.  Columns n..npad-1 are set to zero (the
+// Jacobi sweeps run over npad columns without tests), and so are the padding
+// rows D chiL .. mp-1.
+template <typename R, int D>
 __device__ void form_theta(R* Xr, R* Xi, int ldp, int npad, int mp, const typename CT<R>::T* Bl,
                            const typename CT<R>::T* Br, const typename CT<R>::T* Bs_in, int chiL,
                            int chiM, int chiR, const typename CT<R>::T* G, const double* lamL,
                            bool weighted) {
   typedef typename CT<R>::T Tc;
-  const int n2 = 2 * chiR;
+  const int n2 = D * chiR;
   if (npad > n2) {
     const int w = npad - n2;
-    for (int i = threadIdx.x; i < 2 * chiL * w; i += blockDim.x) {
+    for (int i = threadIdx.x; i < D * chiL * w; i += blockDim.x) {
       const int r = i / w, c = n2 + (i - r * w);
       Xr[r * ldp + c] = (R)0;
       Xi[r * ldp + c] = (R)0;
     }
   }
-  for (int i = threadIdx.x; i < (mp - 2 * chiL) * npad; i += blockDim.x) {
-    const int r = 2 * chiL + i / npad, c = i - (i / npad) * npad;
+  for (int i = threadIdx.x; i < (mp - D * chiL) * npad; i += blockDim.x) {
+    const int r = D * chiL + i / npad, c = i - (i / npad) * npad;
     Xr[r * ldp + c] = (R)0;
     Xi[r * ldp + c] = (R)0;
   }
@@ -97,6 +100,40 @@ __device__ void form_theta(R* Xr, R* Xi, int ldp, int npad, int mp, const typena
     __syncthreads();
   } else {
     Bs = Br;  // no room to stage: read B_{b+1} through L1
+  }
+  if constexpr (D != 2) {
+    for (int idx = threadIdx.x; idx < chiL * chiR; idx += blockDim.x) {
+      const int a = idx / chiR, c = idx - a * chiR;
+      Tc p[D * D];
+#pragma unroll
+      for (int v = 0; v < D * D; ++v) p[v] = czero<Tc>();
+      const Tc* la = Bl + (D * a) * chiM;
+      for (int mu = 0; mu < chiM; ++mu) {
+        Tc x[D], y[D];
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+          x[s] = la[s * chiM + mu];
+          y[s] = Bs[mu * n2 + s * chiR + c];
+        }
+#pragma unroll
+        for (int s = 0; s < D; ++s)
+#pragma unroll
+          for (int t = 0; t < D; ++t) cfma(p[s * D + t], x[s], y[t]);
+      }
+      const R w = weighted ? (R)lamL[a] : (R)1;
+      for (int sp = 0; sp < D; ++sp) {
+        for (int tp = 0; tp < D; ++tp) {
+          const Tc* g = G + (sp * D + tp) * (D * D);
+          Tc v = czero<Tc>();
+#pragma unroll
+          for (int u = 0; u < D * D; ++u) cfma(v, g[u], p[u]);
+          const int o = (D * a + sp) * ldp + tp * chiR + c;
+          Xr[o] = v.x * w;
+          Xi[o] = v.y * w;
+        }
+      }
+    }
+    return;
   }
   const int ahalf = (chiL + 1) >> 1;
   for (int idx = threadIdx.x; idx < ahalf * chiR; idx += blockDim.x) {
@@ -1160,14 +1197,16 @@ __device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int
   mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
 }
 
-template <typename R>
+// D physical values per site: 2 for pure states (trajectories, QSD), 4 for the
+// vectorised density matrix (Eq. MPDO; only mode 0 is launched with D = 4).
+template <typename R, int D>
 __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondArgs<R> a) {
   typedef typename CT<R>::T Tc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_sig[LT_MAX_DIM];
   __shared__ R s_nrm[LT_MAX_DIM];
   __shared__ int s_perm[LT_MAX_DIM];
-  __shared__ Tc s_gate[16];
+  __shared__ Tc s_gate[D * D * D * D];
   __shared__ double s_lamL[LT_MAX_CHI];
   __shared__ int s_k, s_nrot;
   __shared__ double s_norm, s_wdisc;
@@ -1186,21 +1225,26 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     const int chiM = dm[b];
     const int chiR = b == L - 2 ? 1 : dm[b + 1];
     // the matrix the Jacobi sweeps act on: mJ rows of length nJ
-    const int mJ = mode == 1 ? chiM : 2 * chiL;
-    const int nJ = mode == 2 ? chiM : 2 * chiR;
+    const int mJ = mode == 1 ? chiM : D * chiL;
+    const int nJ = mode == 2 ? chiM : D * chiR;
     bool blocked;
     int npad, mpJ;
     jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ);
-    const int mcap = mode == 1 ? (mpJ > 2 * chiL ? mpJ : 2 * chiL) : mpJ;
+    const int mcap = mode == 1 ? (mpJ > D * chiL ? mpJ : D * chiL) : mpJ;
     const int ldp = npad + 2, ld = nJ + 1;
     const int kmax = mJ < nJ ? (mJ < chi ? mJ : chi) : (nJ < chi ? nJ : chi);
     // workspace check (complex elements); a task that would overrun is skipped
     const long long vrows = (long long)kmax * ld;          // V_k^+
-    const long long stage0 = (long long)chiM * 2 * chiR;   // B_{b+1} staged in V_k^+'s place
-    const long long stage2 = (long long)kmax * (chiL > chiR ? 2 * chiL : 2 * chiR);
-    const long long need = (long long)mcap * ldp +
-                           (mode == 0 ? (vrows > stage0 ? vrows : stage0)
-                                      : vrows + (mode == 2 ? stage2 : 0));
+    const long long stage0 = (long long)chiM * D * chiR;   // B_{b+1} staged in V_k^+'s place
+    const long long stage2 = (long long)kmax * (chiL > chiR ? D * chiL : D * chiR);
+    // the r LQ reflectors (n - j entries each) occupy the same region until V_k^+
+    // is assembled; with D = 2 they never exceed the V_k^+ rows, with D = 4 they do
+    const long long r0 = mJ < nJ ? mJ : nJ;
+    const long long refl = r0 * nJ - r0 * (r0 - 1) / 2;
+    long long tail = mode == 0 ? (vrows > stage0 ? vrows : stage0)
+                               : vrows + (mode == 2 ? stage2 : 0);
+    if (refl > tail) tail = refl;
+    const long long need = (long long)mcap * ldp + tail;
     if (need > a.ws_elems) {
       if (tid == 0) atomicOr(a.err, LT_EBIT_WORKSPACE);
       continue;
@@ -1210,12 +1254,24 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     R* Xr = W;
     R* Xi = W + mcap * ldp;
     Tc* Y = reinterpret_cast<Tc*>(W + 2 * mcap * ldp);
-    if (tid < 16) {
-      if (a.gates) {
-        const double2 g = a.gates[b * 16 + tid];
-        s_gate[tid] = cmk<Tc>(g.x, g.y);
-      } else {
-        s_gate[tid] = cmk<Tc>((tid % 5) == 0 ? 1.0 : 0.0, 0.0);
+    constexpr int D4 = D * D * D * D;
+    if constexpr (D4 <= 32) {
+      if (tid < D4) {
+        if (a.gates) {
+          const double2 g = a.gates[b * D4 + tid];
+          s_gate[tid] = cmk<Tc>(g.x, g.y);
+        } else {
+          s_gate[tid] = cmk<Tc>((tid % (D * D + 1)) == 0 ? 1.0 : 0.0, 0.0);
+        }
+      }
+    } else {
+      for (int i = tid; i < D4; i += blockDim.x) {
+        if (a.gates) {
+          const double2 g = a.gates[b * D4 + i];
+          s_gate[i] = cmk<Tc>(g.x, g.y);
+        } else {
+          s_gate[i] = cmk<Tc>((i % (D * D + 1)) == 0 ? 1.0 : 0.0, 0.0);
+        }
       }
     }
     for (int i = tid; i < chiL; i += blockDim.x)
@@ -1223,7 +1279,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     if (tid == 0) s_nrot = 0;
     __syncthreads();
     if (mode == 0) {
-      form_theta<R>(Xr, Xi, ldp, npad, mpJ, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
+      form_theta<R, D>(Xr, Xi, ldp, npad, mpJ, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
     } else {
       // one-site matrix, zero-padded to mpJ x npad
       for (int i = tid; i < mpJ * npad; i += blockDim.x) {
@@ -1231,7 +1287,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
         Tc v = czero<Tc>();
         if (r < mJ && c < nJ) {
           if (mode == 1) v = Br[r * nJ + c];
-          else v = cscale(Bl[r * nJ + c], (R)s_lamL[r >> 1]);
+          else v = cscale(Bl[r * nJ + c], (R)s_lamL[D == 2 ? r >> 1 : r / D]);
         }
         Xr[r * ldp + c] = v.x;
         Xi[r * ldp + c] = v.y;
@@ -1335,8 +1391,8 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
           double fl = 4.0 * dr_ * dr_ * (sweeps + 1) + 8.0 * dr_ * pairs + 24.0 * dr_ * s_nrot;
           fl += 16.0 * (double)(sum_prod(mJ - 1, nJ, rr) + sum_prod(mJ, rr - 1, rr) +
                                 (long long)k * sum_prod(nJ, 1, rr, true));
-          const double mL = 2.0 * chiL, nR = 2.0 * chiR;
-          if (mode == 0) fl += 8.0 * mL * nR * (chiM + 4) + 8.0 * mL * k * nR;
+          const double mL = (double)D * chiL, nR = (double)D * chiR;
+          if (mode == 0) fl += 8.0 * mL * nR * (chiM + D * D) + 8.0 * mL * k * nR;
           else if (mode == 1) fl += 8.0 * mL * nR * chiM + 8.0 * mL * k * nR;
           else fl += 8.0 * mL * chiM * k + 8.0 * k * chiM * nR;
           atomicAdd(a.counters + 0, 1ull);
@@ -1366,9 +1422,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
       // B_b <- theta~ V_k (/ |S_k| in mode 0), B_{b+1} <- V_k^+
-      form_theta<R>(Xr, Xi, ldp, nJ, 2 * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL, false);
+      form_theta<R, D>(Xr, Xi, ldp, nJ, D * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL,
+                       false);
       __syncthreads();
-      const int m = 2 * chiL;
+      const int m = D * chiL;
       const R invn = mode == 0 && !a.keep_norm ? (R)(1.0 / s_norm) : (R)1;
       const int rq = (m + 3) >> 2;
       for (int idx = tid; idx < rq * k; idx += blockDim.x) {
@@ -1396,7 +1453,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     } else {
       // B_b <- B_b V_k / |S_k| (2chi_{b-1} x k), staged, then written
       Tc* St = Y + k * ld;
-      const int m = 2 * chiL, nR = 2 * chiR;
+      const int m = D * chiL, nR = D * chiR;
       const R invn = (R)(1.0 / s_norm);
       for (int idx = tid; idx < m * k; idx += blockDim.x) {
         const int r = idx / k, j = idx - r * k;
@@ -1966,6 +2023,148 @@ __global__ void __launch_bounds__(128) qsd_noise_kernel(typename CT<R>::T* B, co
   }
 }
 
+// ---- traces of the vectorised density matrix (Sec. 3.1) -------------------------------
+// Tr(O rho) of a product operator O contracts |rho>> with one vector per site,
+// o[2n + n'] = O[n', n]: identity (1,0,0,1), n (0,0,0,1), sigma+ = |1><0| (0,1,0,0),
+// sigma- = |0><1| (0,0,1,0), parity (1,0,0,-1).  With T_i(o) = sum_m o[m] B_i[:, m, :]
+// a CTA per chain builds the right vectors R_i = T_i(id) R_{i+1} (R_L = 1) and the
+// left vectors L_{i+1} = L_i T_i(id) (L_0 = 1) in its scratch, Tr rho = R_0, and
+//   <n_i> = Re(L_i T_i(n) R_{i+1} / Tr rho),
+//   C_ij  = L_i T_i(s+) [prod_{i<l<j} T_l(parity)] T_j(s-) R_{j+1} / Tr rho  (i < j),
+// C_ji = conj(C_ij), C_ii = <n_i> (Jordan-Wigner string as for pure states).  The
+// scale of |rho>> is arbitrary (each bond update fixes its Hilbert-Schmidt norm),
+// so only these ratios are physical.  Every contraction accumulates in double
+// precision in a fixed order, so results do not depend on the grid.
+static_assert(LT_MAX_CHI <= LT_BLOCK, "one vector element per thread");
+
+__device__ __forceinline__ double2 block_sum_c2(double2 v, double2* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    v.x += __shfl_xor_sync(FULL, v.x, o);
+    v.y += __shfl_xor_sync(FULL, v.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    s.x += red[w].x;
+    s.y += red[w].y;
+  }
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ void zfma(double2& acc, double2 x, double yr, double yi) {
+  acc.x = fma(x.x, yr, fma(-x.y, yi, acc.x));
+  acc.y = fma(x.x, yi, fma(x.y, yr, acc.y));
+}
+
+// Re(num / den)
+__device__ __forceinline__ double re_ratio(double2 num, double2 den) {
+  return (num.x * den.x + num.y * den.y) / (den.x * den.x + den.y * den.y);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(LT_BLOCK) mpdo_trace_kernel(MpdoArgs a) {
+  typedef typename CT<R>::T Tc;
+  __shared__ double2 s_v[LT_MAX_CHI];
+  __shared__ double2 s_red[LT_BLOCK / 32];
+  const int L = a.L, chi = a.chi, tid = threadIdx.x;
+  double2* Rv = a.scratch + (long long)blockIdx.x * a.stride;  // [L + 1][chi]
+  double2* Lv = Rv + (long long)(L + 1) * chi;                 // [L + 1][chi]
+  for (int t = blockIdx.x; t < a.n_traj; t += gridDim.x) {
+    const int* dm = a.dims + (long long)t * (L - 1);
+    const Tc* Bt = reinterpret_cast<const Tc*>(a.B) + (long long)t * L * a.slot;
+    if (tid == 0) {
+      Rv[(long long)L * chi] = make_double2(1.0, 0.0);
+      Lv[0] = make_double2(1.0, 0.0);
+    }
+    __syncthreads();
+    for (int i = L - 1; i >= 0; --i) {
+      const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+      const Tc* Bi = Bt + (long long)i * a.slot;
+      if (tid < cl) {
+        const Tc* row = Bi + (long long)tid * 4 * cr;  // B_i[x][m][c] at (4x + m) cr + c
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = 0; c < cr; ++c) {
+          const Tc b0 = row[c], b3 = row[3 * cr + c];
+          zfma(acc, Rv[(long long)(i + 1) * chi + c], (double)b0.x + (double)b3.x,
+               (double)b0.y + (double)b3.y);
+        }
+        Rv[(long long)i * chi + tid] = acc;
+      }
+      __syncthreads();
+    }
+    const double2 tr = Rv[0];
+    for (int i = 0; i < L; ++i) {
+      const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+      const Tc* Bi = Bt + (long long)i * a.slot;
+      double2 part = make_double2(0.0, 0.0);
+      if (tid < cr) {
+        double2 nxt = make_double2(0.0, 0.0), num = make_double2(0.0, 0.0);
+        for (int x = 0; x < cl; ++x) {
+          const double2 l = Lv[(long long)i * chi + x];
+          const Tc b0 = Bi[(long long)(4 * x) * cr + tid], b3 = Bi[(long long)(4 * x + 3) * cr + tid];
+          zfma(num, l, b3.x, b3.y);
+          zfma(nxt, l, (double)b0.x + (double)b3.x, (double)b0.y + (double)b3.y);
+        }
+        Lv[(long long)(i + 1) * chi + tid] = nxt;
+        const double2 r = Rv[(long long)(i + 1) * chi + tid];
+        zfma(part, num, r.x, r.y);
+      }
+      const double2 tot = block_sum_c2(part, s_red);
+      if (tid == 0) {
+        const double n = re_ratio(tot, tr);
+        a.density[(long long)t * L + i] = n;
+        if (a.corr) a.corr[((long long)t * L + i) * L + i] = make_double2(n, 0.0);
+      }
+    }
+    if (a.corr) {
+      for (int i = 0; i + 1 < L; ++i) {
+        const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+        const Tc* Bi = Bt + (long long)i * a.slot;
+        if (tid < cr) {
+          double2 v = make_double2(0.0, 0.0);
+          for (int x = 0; x < cl; ++x) {
+            const Tc b1 = Bi[(long long)(4 * x + 1) * cr + tid];
+            zfma(v, Lv[(long long)i * chi + x], b1.x, b1.y);
+          }
+          s_v[tid] = v;
+        }
+        __syncthreads();
+        for (int j = i + 1; j < L; ++j) {
+          const int jl = dm[j - 1], jr = j == L - 1 ? 1 : dm[j];
+          const Tc* Bj = Bt + (long long)j * a.slot;
+          double2 part = make_double2(0.0, 0.0), nv = make_double2(0.0, 0.0);
+          if (tid < jr) {
+            double2 w = make_double2(0.0, 0.0);
+            for (int x = 0; x < jl; ++x) {
+              const double2 v = s_v[x];
+              const Tc b0 = Bj[(long long)(4 * x) * jr + tid], b2 = Bj[(long long)(4 * x + 2) * jr + tid];
+              const Tc b3 = Bj[(long long)(4 * x + 3) * jr + tid];
+              zfma(w, v, b2.x, b2.y);
+              zfma(nv, v, (double)b0.x - (double)b3.x, (double)b0.y - (double)b3.y);
+            }
+            const double2 r = Rv[(long long)(j + 1) * chi + tid];
+            zfma(part, w, r.x, r.y);
+          }
+          const double2 tot = block_sum_c2(part, s_red);  // its barriers end every read of s_v
+          if (tid < jr) s_v[tid] = nv;
+          if (tid == 0) {
+            const double den = tr.x * tr.x + tr.y * tr.y;
+            const double2 cij = make_double2((tot.x * tr.x + tot.y * tr.y) / den,
+                                             (tot.y * tr.x - tot.x * tr.y) / den);
+            a.corr[((long long)t * L + i) * L + j] = cij;
+            a.corr[((long long)t * L + j) * L + i] = make_double2(cij.x, -cij.y);
+          }
+          __syncthreads();
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __global__ void convert_in_kernel(typename CT<R>::T* dst, const double* src, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -1983,17 +2182,20 @@ __global__ void convert_out_kernel(double* dst, const typename CT<R>::T* src, lo
   }
 }
 
+// Product state: |n_i> per site for pure states (d = 2); for the vectorised
+// density matrix (d = 4) the site factor |n_i><n_i| has the one non-zero local
+// index m = 2 n_i + n_i = 3 n_i (Eq. MPDO).
 template <typename R>
 __global__ void init_state_kernel(typename CT<R>::T* B, double* lam, int* dims, double* trunc,
                                   int* evolve, int* channel, const uint8_t* occ, int n_traj,
-                                  int L, int chi, int slot) {
+                                  int L, int chi, int slot, int d) {
   const long long nt = (long long)n_traj * L;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt;
        i += (long long)gridDim.x * blockDim.x) {
     const int traj = (int)(i / L), site = (int)(i - (long long)traj * L);
     typename CT<R>::T* s = B + i * slot;
-    s[0] = cmk<typename CT<R>::T>(occ[site] ? 0.0 : 1.0, 0.0);
-    s[1] = cmk<typename CT<R>::T>(occ[site] ? 1.0 : 0.0, 0.0);
+    const int on = occ[site] ? d - 1 : 0;
+    for (int m = 0; m < d; ++m) s[m] = cmk<typename CT<R>::T>(m == on ? 1.0 : 0.0, 0.0);
     if (site < L - 1) {
       const long long bi = (long long)traj * (L - 1) + site;
       lam[bi * chi] = 1.0;
@@ -2017,11 +2219,12 @@ inline int grid_for(long long n, int block) {
 }  // namespace
 
 // ---- launchers -------------------------------------------------------------------------------
-size_t bond_smem_bytes(int chi, size_t celt) {
+size_t bond_smem_bytes(int chi, size_t celt, int d) {
   // Largest workspace of a task, in complex elements, over the three modes with
-  // every dimension at chi (mirrors the layout of bond_update_kernel): the
-  // Jacobi matrix planar mcap x (npad + 2), V_k^+ k x (nJ + 1), plus the staging
-  // of B_{b+1} (mode 0) or of the new site tensors (mode 2).
+  // every dimension at chi and d physical values per site (mirrors the layout of
+  // bond_update_kernel): the Jacobi matrix planar mcap x (npad + 2), V_k^+
+  // k x (nJ + 1), plus the staging of B_{b+1} (mode 0) or of the new site
+  // tensors (mode 2).
   const bool single = celt == sizeof(float2);
   const size_t epp = single ? BondShape<float>::EPP : BondShape<double>::EPP;
   auto npad_of = [&](size_t m, size_t n) {
@@ -2033,15 +2236,20 @@ size_t bond_smem_bytes(int chi, size_t celt) {
   auto mp_of = [&](size_t m, size_t n) {
     return (single && m >= 32 && n >= 64 && n <= LT_REG_DIM) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
   };
-  const size_t c2 = 2 * (size_t)chi, c1 = chi;
-  // mode 0: theta 2chi x 2chi, V^+ chi x (2chi+1), B_{b+1} staged in V^+'s region
+  const size_t c2 = (size_t)d * chi, c1 = chi;
+  // the LQ reflectors of an m x n matrix (r = min(m, n) of n - j entries) share
+  // the region of V^+ until V^+ is assembled
+  auto refl = [](size_t r, size_t n) { return r * n - r * (r - 1) / 2; };
+  auto mx = [](size_t a, size_t b) { return a > b ? a : b; };
+  // mode 0: theta d chi x d chi, V^+ chi x (d chi+1), B_{b+1} staged in V^+'s region
   const size_t need0 = mp_of(c2, c2) * (npad_of(c2, c2) + 2) +
-                       (c1 * (c2 + 1) > c1 * c2 ? c1 * (c2 + 1) : c1 * c2);
-  // mode 1: B_{b+1} chi x 2chi, later theta~ 2chi x 2chi in the same planes
+                       mx(mx(c1 * (c2 + 1), c1 * c2), refl(c2, c2));
+  // mode 1: B_{b+1} chi x d chi, later theta~ d chi x d chi in the same planes
   const size_t mcap1 = mp_of(c1, c2) > c2 ? mp_of(c1, c2) : c2;
-  const size_t need1 = mcap1 * (npad_of(c1, c2) + 2) + c1 * (c2 + 1);
-  // mode 2: Lambda B_b 2chi x chi, V^+ chi x (chi+1), staged tensors chi x 2chi
-  const size_t need2 = mp_of(c2, c1) * (npad_of(c2, c1) + 2) + c1 * (c1 + 1) + c1 * c2;
+  const size_t need1 = mcap1 * (npad_of(c1, c2) + 2) + mx(c1 * (c2 + 1), refl(c1, c2));
+  // mode 2: Lambda B_b d chi x chi, V^+ chi x (chi+1), staged tensors chi x d chi
+  const size_t need2 =
+      mp_of(c2, c1) * (npad_of(c2, c1) + 2) + mx(c1 * (c1 + 1) + c1 * c2, refl(c1, c1));
   size_t need = need0 > need1 ? need0 : need1;
   need = need > need2 ? need : need2;
   return need * celt;
@@ -2058,7 +2266,7 @@ long long env_grid_cap(int L, int chi, size_t celt, int num_sms) {
   return cap > num_sms ? cap : num_sms;
 }
 
-template <typename R>
+template <typename R, int D>
 static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0,
                                  int nb, const double2* gates, int mode) {
   BondArgs<R> a;
@@ -2072,7 +2280,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.nb = nb;
   a.gates = gates;
   a.mode = mode;
-  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt) / c->celt);
+  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt, D) / c->celt);
   a.L = c->L;
   a.chi = c->chi;
   a.slot = c->slot;
@@ -2087,15 +2295,20 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.counters = c->counters;
   a.keep_norm = c->method == LT_QSD && mode == 0;
   a.logw = c->method == LT_QSD && mode == 2 ? c->logw : nullptr;
-  bond_update_kernel<R><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0, c->stream>>>(a);
+  bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0,
+                             c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_bond(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0, int nb,
                         const double2* gates, int mode) {
-  if (c->prec == LT_MIXED) return launch_bond_t<float>(c, trajs, n_trajs, bond0, nb, gates, mode);
-  return launch_bond_t<double>(c, trajs, n_trajs, bond0, nb, gates, mode);
+  if (c->d == 4) {
+    if (c->prec == LT_MIXED) return launch_bond_t<float, 4>(c, trajs, n_trajs, bond0, nb, gates, mode);
+    return launch_bond_t<double, 4>(c, trajs, n_trajs, bond0, nb, gates, mode);
+  }
+  if (c->prec == LT_MIXED) return launch_bond_t<float, 2>(c, trajs, n_trajs, bond0, nb, gates, mode);
+  return launch_bond_t<double, 2>(c, trajs, n_trajs, bond0, nb, gates, mode);
 }
 
 static EnvArgs env_args(lt_ctx_s* c) {
@@ -2142,6 +2355,26 @@ cudaError_t launch_corr(lt_ctx_s* c) {
   EnvArgs a = env_args(c);
   if (c->prec == LT_MIXED) corr_kernel<float><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
   else corr_kernel<double><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+size_t mpdo_scratch_bytes(int L, int chi) { return 2 * ((size_t)L + 1) * (size_t)chi * sizeof(double2); }
+
+cudaError_t launch_mpdo_trace(lt_ctx_s* c, bool corr) {
+  MpdoArgs a;
+  a.B = c->B;
+  a.dims = c->dims;
+  a.L = c->L;
+  a.chi = c->chi;
+  a.slot = c->slot;
+  a.n_traj = c->n_traj;
+  a.scratch = reinterpret_cast<double2*>(c->env_scratch);
+  a.stride = (long long)(c->env_scratch_stride * c->celt / sizeof(double2));
+  a.density = c->density;
+  a.corr = corr ? c->corr : nullptr;
+  if (c->prec == LT_MIXED) mpdo_trace_kernel<float><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
+  else mpdo_trace_kernel<double><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
 }
@@ -2224,18 +2457,27 @@ cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev) {
   if (c->prec == LT_MIXED)
     init_state_kernel<float><<<grid_for(nt, 256), 256, 0, c->stream>>>(
         reinterpret_cast<float2*>(c->B), c->lam, c->dims, c->trunc, c->evolve, c->channel, occ_dev,
-        c->n_traj, c->L, c->chi, c->slot);
+        c->n_traj, c->L, c->chi, c->slot, c->d);
   else
     init_state_kernel<double><<<grid_for(nt, 256), 256, 0, c->stream>>>(
         reinterpret_cast<double2*>(c->B), c->lam, c->dims, c->trunc, c->evolve, c->channel, occ_dev,
-        c->n_traj, c->L, c->chi, c->slot);
+        c->n_traj, c->L, c->chi, c->slot, c->d);
   c->launches++;
   return cudaGetLastError();
 }
 
+template <typename R, int D>
+static cudaError_t bond_attributes(size_t limit, size_t smem, int* occ) {
+  cudaError_t e = cudaFuncSetAttribute(bond_update_kernel<R, D>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bond_update_kernel<R, D>,
+                                                       BondShape<R>::NT, smem);
+}
+
 // attribute setup and occupancy for the bond kernel (called once per context)
 cudaError_t configure_bond(lt_ctx_s* c) {
-  const size_t need = bond_smem_bytes(c->chi, c->celt);
+  const size_t need = bond_smem_bytes(c->chi, c->celt, c->d);
   const size_t limit = 200 * 1024;
   c->bond_use_smem = need <= limit;
   c->bond_smem = c->bond_use_smem ? need : 0;
@@ -2245,19 +2487,12 @@ cudaError_t configure_bond(lt_ctx_s* c) {
   // every context in the process: it is raised to the most any context may
   // request (limit), never lowered to one context's need, so contexts of
   // different chi_max can live side by side.
-  if (c->prec == LT_MIXED) {
-    e = cudaFuncSetAttribute(bond_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)limit);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<float>,
-                                                      BondShape<float>::NT, c->bond_smem);
-  } else {
-    e = cudaFuncSetAttribute(bond_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)limit);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bond_update_kernel<double>,
-                                                      BondShape<double>::NT, c->bond_smem);
-  }
+  if (c->d == 4)
+    e = c->prec == LT_MIXED ? bond_attributes<float, 4>(limit, c->bond_smem, &occ)
+                            : bond_attributes<double, 4>(limit, c->bond_smem, &occ);
+  else
+    e = c->prec == LT_MIXED ? bond_attributes<float, 2>(limit, c->bond_smem, &occ)
+                            : bond_attributes<double, 2>(limit, c->bond_smem, &occ);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   c->bond_grid = occ * c->num_sms;

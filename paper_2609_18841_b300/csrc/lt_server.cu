@@ -63,19 +63,21 @@ namespace {
 uint64_t context_bytes(const lt_config* cfg, int num_sms) {
   const uint64_t L = cfg->L, chi = cfg->chi_max, nt = cfg->n_traj, nb = L - 1;
   const uint64_t celt = cfg->precision == LT_MIXED ? 8 : 16;
-  const uint64_t slot = 2 * chi * chi;
+  const uint64_t d = cfg->method == LT_MPDO ? 4 : 2;
+  const uint64_t slot = d * chi * chi;
   uint64_t b = nt * L * slot * celt;                       // site tensors
   b += nt * nb * chi * 8 + nt * nb * 4 + nt * nb * 8;      // Lambda, dims, truncation
   b += nt * 4 * 5 + 2 * 4;                                 // flags, channels, lists, counts
   b += nt * L * 8 + nt * 8 + nt * 3 * L * 8 + 3 * L * 8;   // density, log weights, rates, rates table
-  b += 4 + 64 * 4 + LT_NCOUNTERS * 8 + 8 * nb * 16 * 16;   // error word, histogram, counters, gates
+  b += 4 + 64 * 4 + LT_NCOUNTERS * 8 + 8 * nb * d * d * d * d * 16;  // error word, histogram, counters, gates
   b += (2 * L * L + 2 * L) * 8;                            // reduction buffer
-  const uint64_t need = bond_smem_bytes((int)chi, celt);
+  const uint64_t need = bond_smem_bytes((int)chi, celt, (int)d);
   if (need > 200 * 1024) b += 2ull * num_sms * need;       // bond scratch when not in shared memory
   uint64_t env_grid = nt < 8ull * num_sms ? nt : 8ull * num_sms;
   const uint64_t cap = (uint64_t)env_grid_cap((int)L, (int)chi, celt, num_sms);
   if (env_grid > cap) env_grid = cap;
-  b += env_grid * env_scratch_elems((int)L, (int)chi) * celt;
+  b += env_grid * (d == 4 ? (uint64_t)mpdo_scratch_bytes((int)L, (int)chi)
+                          : env_scratch_elems((int)L, (int)chi) * celt);
   return b;
 }
 

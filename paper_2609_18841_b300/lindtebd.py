@@ -202,7 +202,8 @@ def lt_get_stats(ctx, L, n_traj):
 
 
 def lt_set_state(ctx, traj0, dims, lam, B):
-    """dims [n, L-1] int32, lam [n, L-1, chi] float64, B [n, L, 2 chi^2] complex128."""
+    """dims [n, L-1] int32, lam [n, L-1, chi] float64, B [n, L, d chi^2] complex128
+    (d = 2 for pure states, 4 for the vectorised density matrix)."""
     dims = np.ascontiguousarray(dims, np.int32)
     lam = np.ascontiguousarray(lam, np.float64)
     B = np.ascontiguousarray(B, np.complex128)
@@ -210,10 +211,10 @@ def lt_set_state(ctx, traj0, dims, lam, B):
            "lt_set_state", ctx)
 
 
-def lt_get_state(ctx, traj0, n, L, chi):
+def lt_get_state(ctx, traj0, n, L, chi, d=2):
     dims = np.empty((n, L - 1), np.int32)
     lam = np.empty((n, L - 1, chi))
-    B = np.empty((n, L, 2 * chi * chi), np.complex128)
+    B = np.empty((n, L, d * chi * chi), np.complex128)
     _check(_lib.lt_get_state(ctx, traj0, n, _ptr(dims), _ptr(lam), _ptr(B)), "lt_get_state", ctx)
     return dims, lam, B
 
@@ -262,12 +263,12 @@ def lt_get_step(ctx):
 
 
 # ---- packing helpers: list-of-tensors MPS <-> the library's padded layout ---------------
-def pack_state(mps_list, L, chi):
-    """mps_list: per trajectory (B list of (chi_l, 2, chi_r), lam list, dims)."""
+def pack_state(mps_list, L, chi, d=2):
+    """mps_list: per trajectory (B list of (chi_l, d, chi_r), lam list, dims)."""
     n = len(mps_list)
     dims = np.zeros((n, L - 1), np.int32)
     lam = np.zeros((n, L - 1, chi))
-    Bp = np.zeros((n, L, 2 * chi * chi), np.complex128)
+    Bp = np.zeros((n, L, d * chi * chi), np.complex128)
     for t, (B, lm, dm) in enumerate(mps_list):
         dims[t] = dm
         for b in range(L - 1):
@@ -278,10 +279,10 @@ def pack_state(mps_list, L, chi):
     return dims, lam, Bp
 
 
-def unpack_state(dims, lam, Bp, L):
+def unpack_state(dims, lam, Bp, L, d=2):
     """Inverse of pack_state for one trajectory."""
     full = [1] + [int(x) for x in dims] + [1]
-    B = [Bp[i, :full[i] * 2 * full[i + 1]].reshape(full[i], 2, full[i + 1]) for i in range(L)]
+    B = [Bp[i, :full[i] * d * full[i + 1]].reshape(full[i], d, full[i + 1]) for i in range(L)]
     lm = [lam[b, :full[b + 1]] for b in range(L - 1)]
     return B, lm
 
@@ -291,6 +292,7 @@ class Ensemble:
 
     def __init__(self, L, chi_max, n_traj, **kw):
         self.L, self.chi, self.n_traj = L, chi_max, n_traj
+        self.d = 4 if kw.get("method", LT_TRAJ) == LT_MPDO else 2
         self.ctx = lt_create(L, chi_max, n_traj, **kw)
 
     def close(self):
@@ -335,11 +337,11 @@ class Ensemble:
         return lt_get_stats(self.ctx, self.L, self.n_traj)
 
     def set_state(self, traj0, mps_list):
-        dims, lam, B = pack_state(mps_list, self.L, self.chi)
+        dims, lam, B = pack_state(mps_list, self.L, self.chi, self.d)
         lt_set_state(self.ctx, traj0, dims, lam, B)
 
     def get_state(self, traj0, n):
-        return lt_get_state(self.ctx, traj0, n, self.L, self.chi)
+        return lt_get_state(self.ctx, traj0, n, self.L, self.chi, self.d)
 
     def launches(self):
         return lt_launch_count(self.ctx)
