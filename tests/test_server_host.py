@@ -20,6 +20,14 @@ def test_context_bytes_scales_with_the_ensemble():
         lt.lt_context_bytes(64, 129, 16, **base)
 
 
+def test_context_bytes_of_a_vectorised_density_matrix():
+    # four local values per site: the site tensors are twice as large
+    base = dict(precision=lt.LT_MIXED, num_sms=148)
+    traj = lt.lt_context_bytes(32, 64, 8, **base)
+    rho = lt.lt_context_bytes(32, 64, 8, method=lt.LT_MPDO, **base)
+    assert rho - traj >= 8 * 32 * 2 * 64 * 64 * 8
+
+
 @pytest.mark.parametrize("budget,used,max_active,n_active,queue,want", [
     (100, 0, 8, 0, [30, 30, 30, 30], 3),     # budget stops the fourth
     (100, 50, 8, 1, [30, 10], 2),            # both fit in order (80, then 90)
