@@ -1230,7 +1230,18 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     bool blocked;
     int npad, mpJ;
     jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ);
-    const int mcap = mode == 1 ? (mpJ > D * chiL ? mpJ : D * chiL) : mpJ;
+    // two-level Householder preconditioning; the Jacobi then acts on the r x r
+    // upper-triangular factor, whose window (mp2 x npad2) can have more rows than
+    // the mJ x nJ layout: a wide matrix (nJ > LT_REG_DIM, rows rounded to even)
+    // whose factor takes the blocked layout (rows rounded to 8).  The planes hold
+    // both, plus in mode 1 the D chi_{b-1} rows of theta~ formed afterwards, and
+    // every row below mJ is zero from the formation on.
+    const int rr = mJ < nJ ? mJ : nJ;
+    bool blk2;
+    int npad2, mp2;
+    jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
+    const int mpad = mpJ > mp2 ? mpJ : mp2;
+    const int mcap = mode == 1 ? (mpad > D * chiL ? mpad : D * chiL) : mpad;
     const int ldp = npad + 2, ld = nJ + 1;
     const int kmax = mJ < nJ ? (mJ < chi ? mJ : chi) : (nJ < chi ? nJ : chi);
     // workspace check (complex elements); a task that would overrun is skipped
@@ -1245,7 +1256,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
                                : vrows + (mode == 2 ? stage2 : 0);
     if (refl > tail) tail = refl;
     const long long need = (long long)mcap * ldp + tail;
-    if (need > a.ws_elems) {
+    if (need > a.ws_elems || npad2 > npad) {
       if (tid == 0) atomicOr(a.err, LT_EBIT_WORKSPACE);
       continue;
     }
@@ -1279,10 +1290,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     if (tid == 0) s_nrot = 0;
     __syncthreads();
     if (mode == 0) {
-      form_theta<R, D>(Xr, Xi, ldp, npad, mpJ, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
+      form_theta<R, D>(Xr, Xi, ldp, npad, mpad, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
     } else {
-      // one-site matrix, zero-padded to mpJ x npad
-      for (int i = tid; i < mpJ * npad; i += blockDim.x) {
+      // one-site matrix, zero-padded to mpad x npad
+      for (int i = tid; i < mpad * npad; i += blockDim.x) {
         const int r = i / npad, c = i - r * npad;
         Tc v = czero<Tc>();
         if (r < mJ && c < nJ) {
@@ -1293,12 +1304,6 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
         Xi[r * ldp + c] = v.y;
       }
     }
-    // two-level Householder preconditioning; the Jacobi then acts on the r x r
-    // upper-triangular factor (its layout fits inside the one chosen for mJ x nJ)
-    const int rr = mJ < nJ ? mJ : nJ;
-    bool blk2;
-    int npad2, mp2;
-    jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
     // register paths for the sizes they hold (every task up to chi_max = 64)
     const bool reg = sizeof(R) == 4 && mJ <= LT_REG_DIM && nJ <= LT_REG_DIM && kmax <= LT_REG_CHI;
     if constexpr (sizeof(R) == 4) {

@@ -110,7 +110,7 @@ def test_ragged_chains_from_different_states():
     starts = []
     for k, occ in enumerate(occs):
         cfg = cfg_of(L, chi, loss=0.2, gain=0.1 + 0.05 * k, deph=0.05, occ=occ)
-        m = mpdo.run_mpdo(cfg, 4 + k)["state"]
+        m = mpdo.run_mpdo(cfg, (1, 1, 2)[k])["state"]
         starts.append(([b.copy() for b in m.B], [x.copy() for x in m.lam], m.bond_dims()))
     # one context holds all three chains and applies one set of rates (those
     # of chain 0) to all of them from here on
@@ -194,3 +194,34 @@ def test_mpdo_checkpoint_and_method_errors(tmp_path):
         c.step(4)
         dc = c.density(per_traj=True)[2]
     assert np.array_equal(da, dc)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_wide_theta_whose_factor_takes_the_blocked_rows(precision, tol):
+    # bond 3 of an 8-site chain with dims 19 | 40 | 36: theta is 76 x 144 (wider
+    # than the register path holds) and its 76 x 76 factor takes the blocked
+    # Jacobi layout with rows rounded up to 80; a synthetic (non-physical) state
+    from paper_2609_18841_b300.lindtebd import unpack_state
+    lt = _lt()
+    L, chi = 8, 64
+    dims = [4, 16, 19, 40, 36, 16, 4]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=6, d=4, dims=dims)
+    cut = 1e-12 if precision == "fp64" else 1e-6
+    cfg = cfg_of(L, chi, loss=0.1, gain=0.05, cut=cut)
+    ref = mpdo.MPDO(cfg)
+    ref.B, ref.lam = [b.copy() for b in B], [x.copy() for x in lam]
+    ref.apply_layer(1, mpdo.bond_gates(cfg, 0.05))
+    prec = lt.LT_FP64 if precision == "fp64" else lt.LT_MIXED
+    with ensemble(cfg, 1, prec) as e:
+        e.set_state(0, [(B, lam, dims)])
+        e.apply_layer(1, 0.05)
+        gd, gl, gB = e.get_state(0, 1)
+    gBs, gls = unpack_state(gd[0], gl[0], gB[0], L, d=4)
+    for b in (1, 3, 5):
+        X = np.tensordot(ref.B[b], ref.B[b + 1], axes=(2, 0)).reshape(4 * ref.B[b].shape[0], -1)
+        Y = np.tensordot(gBs[b], gBs[b + 1], axes=(2, 0)).reshape(4 * gBs[b].shape[0], -1)
+        w = np.repeat(ref.lam[b - 1], 4)[:, None]
+        err = np.abs(w * (Y - X)).max() / np.abs(w * X).max()
+        assert err < tol, "bond %d: relative error %.2e" % (b, err)
+    if precision == "fp64":
+        assert list(gd[0]) == ref.bond_dims()

@@ -328,3 +328,48 @@ def test_chi128_mixed_two_steps():
         gpu_steps(ens, cfg, 2, replay=res["jumps"])
         _, _, dens = ens.density(per_traj=True)
     assert_close(dens, res["density"], 2e-5, "chi 128 mixed density")
+
+
+def _two_site_blocks(B, lam, bonds, d):
+    """Lambda_{b-1} B_b B_{b+1} as (d chi_{b-1}) x (d chi_{b+1}) matrices: after a
+    two-site update this is theta~ V_k V_k^+ / |S_k| weighted, independent of the
+    phases (and of rotations within degenerate subspaces) of the singular vectors."""
+    out = {}
+    for b in bonds:
+        X = np.tensordot(B[b], B[b + 1], axes=(2, 0))
+        X = X.reshape(X.shape[0] * d, -1)
+        w = lam[b - 1] if b > 0 else np.ones(1)
+        out[b] = X * np.repeat(w, d)[:, None]
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_wide_theta_whose_factor_takes_the_blocked_rows(precision, tol):
+    # bond 7 of a 16-site chain with dims 38 | 100 | 70: theta is 76 x 140, too
+    # wide for the register path, while its 76 x 76 triangular factor takes the
+    # blocked Jacobi layout, whose rows are rounded up to 80
+    from paper_2609_18841_b300.lindtebd import unpack_state
+    lt = _lt()
+    L, chi = 16, 128
+    dims = [min(2 ** (b + 1), 2 ** (L - b - 1), 64) for b in range(L - 1)]
+    dims[6], dims[7], dims[8] = 38, 100, 70
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=5, dims=dims)
+    cut = 1e-12 if precision == "fp64" else 1e-6
+    cfg = tebd.TrajectoryConfig(L, J=1.0, dt=0.05, chi_max=chi, svd_cut=cut, gamma_loss=0.2,
+                                occupation=workloads.occupation(L, "neel"))
+    ref = tebd.Trajectory.from_tensors(cfg, B, lam)
+    ref.apply_layer(1, cfg.gates(0.05))
+    prec = lt.LT_FP64 if precision == "fp64" else lt.LT_MIXED
+    with lt.Ensemble(L, chi, 1, precision=prec, dt=0.05, gamma_loss=0.2, svd_cut=cut) as e:
+        e.set_state(0, [(B, lam, dims)])
+        e.apply_layer(1, 0.05)
+        gd, gl, gB = e.get_state(0, 1)
+    gBs, gls = unpack_state(gd[0], gl[0], gB[0], L)
+    bonds = list(range(1, L - 1, 2))
+    want = _two_site_blocks(ref.B, ref.lam, bonds, 2)
+    got = _two_site_blocks(gBs, gls, bonds, 2)
+    for b in bonds:
+        err = np.abs(got[b] - want[b]).max() / np.abs(want[b]).max()
+        assert err < tol, "bond %d: relative error %.2e" % (b, err)
+    if precision == "fp64":
+        assert list(gd[0]) == ref.bond_dims()

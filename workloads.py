@@ -62,15 +62,20 @@ def bond_dims(L, chi_max, rng=None, ragged=False, d=2):
     return dims
 
 
-def synthetic_mps(L, chi_max, seed, ragged=False, d=2, decay=8.0):
+def synthetic_mps(L, chi_max, seed, ragged=False, d=2, decay=8.0, dims=None):
     """Random MPS in (approximate) Vidal-Hastings form.
 
     B_i: i.i.d. complex Gaussian entries, made right-canonical by a QR
-    factorisation of the conjugate transpose (rows orthonormal);
+    factorisation of the conjugate transpose (rows orthonormal; needs
+    chi_{i-1} <= d chi_i);
     Lambda_b,a proportional to exp(-a/decay), normalised to sum Lambda^2 = 1.
+    dims: explicit bond dimensions [L-1] instead of drawn ones.
     Returns (B list of (chi_{i-1}, d, chi_i) complex128, lam list, dims)."""
     rng = np.random.default_rng(seed)
-    dims = bond_dims(L, chi_max, rng, ragged, d)
+    if dims is None:
+        dims = bond_dims(L, chi_max, rng, ragged, d)
+    else:
+        dims = np.asarray(dims, dtype=np.int64)
     full = [1] + [int(x) for x in dims] + [1]
     B = []
     for i in range(L):
