@@ -40,7 +40,14 @@ loss or gain raises ValueError.
 
 State update (Eq. Theta in the Hastings form, as for pure states): theta~ =
 G (B_b B_{b+1}), theta = Lambda_{b-1} theta~, SVD, keep k values,
-B_{b+1} <- V_k^+, B_b <- theta~ V_k / ||S_k||, Lambda_b <- S_k / ||S_k||.  The
+B_{b+1} <- V_k^+, B_b <- theta~ V_k / ||S_k||, Lambda_b <- S_k / ||S_k||.
+Truncation keeps the largest values as for pure states, except that it never
+splits a multiplet of equal singular values: rho = rho^+ maps the coherences of
+particle-number difference q onto those of -q, so the Schmidt spectrum of
+|rho>> holds exactly degenerate pairs, and keeping one member of a pair would
+pick an arbitrary vector of the pair and leave a non-Hermitian rho.  k is
+lowered while S_{k-1} - S_k <= MULTIPLET_TOL S_0 (the paper is silent on this;
+it is a reading).  The
 scale of |rho>> is thereby not tracked (the renormalisation fixes its
 Hilbert-Schmidt norm, not its trace), so every observable is a ratio
 Tr(O rho) / Tr rho.
@@ -61,6 +68,17 @@ E_N = np.array([0.0, 0.0, 0.0, 1.0], dtype=complex)
 E_SPLUS = np.array([0.0, 1.0, 0.0, 0.0], dtype=complex)
 E_SMINUS = np.array([0.0, 0.0, 1.0, 0.0], dtype=complex)
 E_PARITY = np.array([1.0, 0.0, 0.0, -1.0], dtype=complex)
+
+# singular values closer than this (relative to the largest) count as one multiplet
+MULTIPLET_TOL = 1e-9
+
+
+def keep_multiplets(S, k, tol=MULTIPLET_TOL):
+    """Largest k' <= k (at least 1) whose cut does not split a multiplet of the
+    descending singular values S."""
+    while 1 < k < len(S) and S[k - 1] - S[k] <= tol * S[0]:
+        k -= 1
+    return k
 
 
 def superop(A, B):
@@ -161,7 +179,7 @@ class MPDO:
         if not S[0] > 0.0:
             raise FloatingPointError("theta vanished at bond %d" % b)
         k = int(np.count_nonzero(S > cfg.svd_cut * S[0]))
-        k = max(1, min(cfg.chi_max, k))
+        k = keep_multiplets(S, max(1, min(cfg.chi_max, k)))
         total = float(np.sum(S ** 2))
         kept = float(np.sum(S[:k] ** 2))
         norm = np.sqrt(kept)

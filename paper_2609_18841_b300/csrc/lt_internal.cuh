@@ -154,6 +154,7 @@ template <typename R> struct BondArgs {
   unsigned long long* counters;  // see lt_get_counters
   int keep_norm;         // mode 0: B_b keeps the factor ||S_k|| (quantum state diffusion)
   double* logw;          // mode 2 at bond 0: += ln ||S||^2 per trajectory, or nullptr
+  double multiplet;      // > 0: k never splits singular values closer than this x sigma_0
 };
 
 struct EnvArgs {

@@ -1375,6 +1375,14 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       }
       int k = s0 > 0.0 ? cnt : 0;
       if (k < 1) k = 1;
+      // vectorised density matrix: never split a multiplet of equal singular
+      // values (the spectrum of |rho>> pairs the coherences q and -q; keeping
+      // one member of a pair would leave rho non-Hermitian and the kept vector
+      // arbitrary).  Every lane walks the same values, so k stays warp-uniform.
+      if (a.multiplet > 0.0 && s0 > 0.0) {
+        const double tol = a.multiplet * sqrt(s0);
+        while (k > 1 && k < rr && sqrt(s_sig[s_perm[k - 1]]) - sqrt(s_sig[s_perm[k]]) <= tol) --k;
+      }
       double kept = 0.0;
       for (int j = lane; j < k; j += 32) kept += s_sig[s_perm[j]];
 #pragma unroll
@@ -2300,6 +2308,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.counters = c->counters;
   a.keep_norm = c->method == LT_QSD && mode == 0;
   a.logw = c->method == LT_QSD && mode == 2 ? c->logw : nullptr;
+  a.multiplet = c->method == LT_MPDO ? (c->prec == LT_MIXED ? 1e-5 : 1e-9) : 0.0;
   bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0,
                              c->stream>>>(a);
   c->launches++;

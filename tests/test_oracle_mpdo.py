@@ -242,3 +242,21 @@ def test_bulk_truncation_is_the_best_rank_k_approximation_of_the_state():
     got = (m.B[0].reshape(4, -1) @ m.B[1].reshape(m.B[1].shape[0], -1)).reshape(16, -1)
     got = (got @ m.B[2].reshape(m.B[2].shape[0], -1)).reshape(-1)
     assert np.abs(got - best).max() < 1e-13
+
+
+def test_truncation_keeps_degenerate_pairs_and_hermiticity():
+    # the Schmidt spectrum of |rho>> comes in equal pairs (coherences q and -q);
+    # with chi_max = 8 the plain cut would split the pair at 7/8 and leave a
+    # non-Hermitian rho (error ~1e-2): the truncation keeps fewer values instead
+    L = 6
+    for chi in (4, 6, 8, 12):
+        cfg = cfg_of(L, dt=0.1, chi=chi, loss=0.3, gain=0.2, deph=0.1, occ="neel")
+        m = mpdo.run_mpdo(cfg, 8)["state"]
+        rho = m.to_dense()
+        rho = rho / np.trace(rho)
+        assert np.abs(rho - rho.conj().T).max() < 1e-12, chi
+        assert max(m.bond_dims()) <= chi
+    cfg = cfg_of(L, dt=0.1, chi=8, loss=0.3, gain=0.2, deph=0.1, occ="neel")
+    assert max(mpdo.run_mpdo(cfg, 8)["bond_dims"]) < 8     # pairs dropped, not split
+    S = np.array([3.0, 2.0, 2.0, 1.0, 1.0, 0.5])
+    assert [mpdo.keep_multiplets(S, k) for k in range(1, 7)] == [1, 1, 3, 3, 5, 6]
