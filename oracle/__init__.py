@@ -16,6 +16,9 @@ Modules
   mpdo     the vectorised density matrix (MPDO, d^2 = 4) under Liouvillian
            TEBD gates (Sec. 3.1, Eqs. Choi, LindbladChoi, Liouvillian, MPDO),
            with traces Tr(O rho) / Tr rho for the observables.
+  purified the locally purified density matrix rho = X X^+ (Sec. 3.2, Eqs.
+           Purified, ThetaPurified, MatrixR, NewPurified): effective-Hamiltonian
+           layers on X with a Kraus index per site, then the R step per site.
   dense    brute-force references: the dense Trotterised state vector, dense
            Lindblad integration of rho, and the correlation-matrix equation of
            motion (Sec. 2.1 Eqs. eqCorr, SoleqCorr; Eq. Lindblad).
