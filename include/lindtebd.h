@@ -69,10 +69,11 @@ typedef enum {
 typedef struct {
   int32_t L;                 /* chain length, 2 <= L <= 1024                       */
   int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 128 (<= 64 for */
-                             /* LT_MPDO, whose theta is 4 chi wide)                */
+                             /* LT_MPDO and LT_PURIFIED, whose theta is 4 chi wide)*/
   int32_t n_traj;            /* trajectories held by this context, >= 1            */
-  int32_t kraus_dim;         /* unused by LT_TRAJ (purified method), set 0         */
-  int32_t method;            /* lt_method; LT_TRAJ, LT_QSD and LT_MPDO are built   */
+  int32_t kraus_dim;         /* LT_PURIFIED: Kraus dimension, 2 (0 selects 2); set */
+                             /* 0 for the other methods                            */
+  int32_t method;            /* lt_method (all four are built)                     */
   int32_t precision;         /* lt_precision                                       */
   int32_t init;              /* lt_init                                            */
   int32_t trotter_order;     /* 1: A(dt) B(dt); 2: A(dt/2) B(dt) A(dt/2)           */
@@ -95,8 +96,10 @@ typedef struct {
  * and set every trajectory to the initial product state (Sec. 4.1: the
  * initial pure state is an eigenvector of rho(0), here a product state); an
  * LT_MPDO chain starts from rho = |n><n| of that product state (local index
- * 3 n_i on every site).  LT_ERR_UNSUPPORTED: LT_PURIFIED; LT_MPDO with
- * chi_max > 64, or with fermionic loss or gain on a bulk site (on the chain
+ * 3 n_i on every site), an LT_PURIFIED chain from X = |n> with Kraus index 0
+ * (s = 2 n_i).  LT_ERR_UNSUPPORTED: LT_MPDO or LT_PURIFIED with chi_max > 64,
+ * LT_PURIFIED with kraus_dim other than 0 or 2, either with fermionic loss or
+ * gain on a bulk site (on the chain
  * ends the Jordan-Wigner string acts as the total parity, which commutes with
  * every state reached from a product state, so c and c^+ act there as the
  * local sigma- and sigma+; in the bulk they would not be local).
@@ -154,6 +157,21 @@ lt_status lt_apply_jumps(lt_ctx ctx, int64_t step, const int32_t* replay,
  * of non-local products). */
 lt_status lt_apply_noise(lt_ctx ctx, int64_t step);
 
+/* The R step of the locally purified density matrix (Sec. 3.2, Eqs. MatrixR,
+ * NewPurified; LT_PURIFIED contexts, LT_ERR_UNSUPPORTED otherwise).  rho = X X^+
+ * with X an MPS over s = 2n + k (physical n, Kraus index k, kraus_dim = 2).  On
+ * every site the Kraus vectors are enlarged to A~ = [A^{.,k} ; sqrt(gamma_c dt)
+ * L_c A^{.,k}] over the site's channels (loss sigma-, gain sigma+, dephasing n),
+ * which turns sum_k A A^+ into the tensor R of Eq. MatrixR (rho -> rho + dt
+ * sum_c gamma_c L_c rho L_c^+ on that site), and replaced by A~ V with V the two
+ * leading eigenvectors of the Lambda_{i-1}-weighted Gram matrix A~^+ W^2 A~ (at
+ * most 8 x 8, W the left Schmidt values: the site's environment in this gauge),
+ * which are the leading eigenvectors of R scaled by sqrt(lambda).  In an
+ * LT_PURIFIED context lt_apply_layer applies exp(-i h_b^eff tau) (x) 1 over the
+ * Kraus indices and keeps the norm change (B_b <- theta~ V_k), and lt_step runs
+ * the layers, then this call. */
+lt_status lt_apply_kraus(lt_ctx ctx);
+
 /* ln <psi|psi> of every unnormalised QSD history, out: [n_traj] (0 for the
  * trajectory method and after lt_set_state). */
 lt_status lt_get_log_weights(lt_ctx ctx, double* out);
@@ -162,7 +180,8 @@ lt_status lt_get_log_weights(lt_ctx ctx, double* out);
  * counter (starting at 0): for LT_TRAJ lt_apply_jumps(step, NULL, NULL) then
  * the layers of the configured Trotter order; for LT_QSD the layers then
  * lt_apply_noise(step); for LT_MPDO the layers only (lt_apply_jumps and
- * lt_apply_noise return LT_ERR_UNSUPPORTED there). */
+ * lt_apply_noise return LT_ERR_UNSUPPORTED there); for LT_PURIFIED the layers
+ * then lt_apply_kraus. */
 lt_status lt_step(lt_ctx ctx, int32_t n_steps);
 
 /* Ensemble density <n_i> = <psi|n_i|psi>/<psi|psi> (exact environments).
@@ -173,7 +192,8 @@ lt_status lt_step(lt_ctx ctx, int32_t n_steps);
  * per_traj holds the normalised <n_i>_t.  For LT_MPDO per_traj holds each
  * chain's Re Tr(n_i rho) / Tr rho, the traces contracting |rho>> with the
  * vectors o[2n + n'] = O[n', n] of each site's operator, and mean/sem run over
- * the chains. */
+ * the chains.  For LT_PURIFIED per_traj holds Tr(n_i X X^+) / Tr(X X^+) =
+ * <X| n_i (x) 1 |X> / <X|X> by exact environments. */
 lt_status lt_measure_density(lt_ctx ctx, double* mean, double* sem, double* per_traj);
 
 /* Correlation matrix C_ij = <c_i^+ c_j> (Sec. 2.1) by transfer matrices with
@@ -193,7 +213,8 @@ lt_status lt_get_stats(lt_ctx ctx, double* trunc_weight, int32_t* bond_dims);
  * B [L * d * chi_max^2] complex128 as interleaved (re, im) doubles, site i at
  * i * d * chi_max^2, holding B_i[a][s][c] row-major over its actual shape
  * (chi_{i-1}, d, chi_i), d = 2 (d = 4 for LT_MPDO, s the local index
- * m = 2n + n').  Dimensions must satisfy 1 <= chi_b <= chi_max.
+ * m = 2n + n', and for LT_PURIFIED, s = 2n + k).  Dimensions must satisfy
+ * 1 <= chi_b <= chi_max.
  * lt_set_state also clears the truncation accumulators and the log weights of
  * those trajectories. */
 lt_status lt_set_state(lt_ctx ctx, int32_t traj0, int32_t n, const int32_t* dims,
@@ -230,7 +251,7 @@ lt_status lt_get_sweep_histogram(lt_ctx ctx, int32_t* sweep_hist, int32_t clear)
 lt_status lt_get_counters(lt_ctx ctx, uint64_t* out, int32_t clear);
 
 /* ---- request server (continuous batching; the paper has no serving layer) ----
- * A request is one ensemble (an lt_config, method LT_TRAJ, LT_QSD or LT_MPDO) run for
+ * A request is one ensemble (an lt_config, any method) run for
  * n_steps time steps.  Each admitted request owns a context and its stream on
  * the current device, so the steps of all active requests are queued side by
  * side and the GPU interleaves their kernels; the ensemble stays resident from

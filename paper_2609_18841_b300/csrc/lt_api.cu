@@ -243,6 +243,28 @@ void build_liouvillian_gates(const lt_ctx_s* c, double tau, std::vector<double2>
   }
 }
 
+// Purified density matrix (Sec. 3.2, Eq. ThetaPurified): the effective-Hamiltonian
+// gate over the physical indices times the identity over the Kraus indices, on
+// s = 2n + k: F[(s_b, s_{b+1}), (t_b, t_{b+1})] = G[(n_b n_{b+1}), (m_b m_{b+1})]
+// delta(k_b, k'_b) delta(k_{b+1}, k'_{b+1}).
+void build_purified_gates(const lt_ctx_s* c, double tau, std::vector<double2>& out) {
+  std::vector<double2> g4;
+  build_gates(c, tau, g4);
+  const int L = c->L;
+  out.assign((size_t)(L - 1) * 256, make_double2(0, 0));
+  for (int b = 0; b < L - 1; ++b)
+    for (int nb = 0; nb < 2; ++nb)
+      for (int kb = 0; kb < 2; ++kb)
+        for (int nc = 0; nc < 2; ++nc)
+          for (int kc = 0; kc < 2; ++kc)
+            for (int mb = 0; mb < 2; ++mb)
+              for (int mc = 0; mc < 2; ++mc) {
+                const int row = (2 * nb + kb) * 4 + (2 * nc + kc);
+                const int col = (2 * mb + kb) * 4 + (2 * mc + kc);
+                out[(size_t)b * 256 + row * 16 + col] = g4[(size_t)b * 16 + (nb * 2 + nc) * 4 + (mb * 2 + mc)];
+              }
+}
+
 lt_status gate_ptr(lt_ctx_s* c, double tau, const double2** out) {
   const size_t per = (size_t)(c->L - 1) * c->d * c->d * c->d * c->d;
   for (size_t i = 0; i < c->gate_taus.size(); ++i)
@@ -252,7 +274,8 @@ lt_status gate_ptr(lt_ctx_s* c, double tau, const double2** out) {
     }
   if (c->gate_taus.size() >= 8) return fail(c, LT_ERR_ARG, "lt_apply_layer", "more than 8 distinct tau values");
   std::vector<double2> h;
-  if (c->d == 4) build_liouvillian_gates(c, tau, h);
+  if (c->method == LT_MPDO) build_liouvillian_gates(c, tau, h);
+  else if (c->method == LT_PURIFIED) build_purified_gates(c, tau, h);
   else build_gates(c, tau, h);
   const size_t i = c->gate_taus.size();
   double2* dst = c->gates + i * per;
@@ -359,11 +382,15 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (!out) return LT_ERR_ARG;
   *out = nullptr;
   if (!cfg) return LT_ERR_ARG;
-  if (cfg->method != LT_TRAJ && cfg->method != LT_QSD && cfg->method != LT_MPDO)
+  if (cfg->method != LT_TRAJ && cfg->method != LT_QSD && cfg->method != LT_MPDO &&
+      cfg->method != LT_PURIFIED)
     return LT_ERR_UNSUPPORTED;
-  // theta of the vectorised density matrix is 4 chi x 4 chi: the two-site
-  // update holds sides up to LT_MAX_DIM
-  if (cfg->method == LT_MPDO && cfg->chi_max > LT_MAX_DIM / 4 && cfg->chi_max <= LT_MAX_CHI)
+  // theta of the vectorised and of the purified density matrix is 4 chi x 4 chi:
+  // the two-site update holds sides up to LT_MAX_DIM; the purified form is built
+  // for a Kraus dimension of 2 (0 selects it)
+  const bool four = cfg->method == LT_MPDO || cfg->method == LT_PURIFIED;
+  if (four && cfg->chi_max > LT_MAX_DIM / 4 && cfg->chi_max <= LT_MAX_CHI) return LT_ERR_UNSUPPORTED;
+  if (cfg->method == LT_PURIFIED && cfg->kraus_dim != 0 && cfg->kraus_dim != 2)
     return LT_ERR_UNSUPPORTED;
   if (cfg->L < 2 || cfg->L > 1024 || cfg->chi_max < 1 || cfg->chi_max > LT_MAX_CHI ||
       cfg->n_traj < 1 || (cfg->precision != LT_FP64 && cfg->precision != LT_MIXED) ||
@@ -410,7 +437,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
     }
     // the vectorised density matrix takes c_i and c_i^+ as local operators on
     // the chain ends only (there the string acts as the total parity)
-    if (c->method == LT_MPDO && c->fermionic && i > 0 && i < L - 1 &&
+    if ((c->method == LT_MPDO || c->method == LT_PURIFIED) && c->fermionic && i > 0 && i < L - 1 &&
         (c->gl[i] > 0.0 || c->gg[i] > 0.0)) {
       delete c;
       return LT_ERR_UNSUPPORTED;
@@ -425,7 +452,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
       default: c->occ[i] = cfg->product_occ[i] ? 1 : 0;
     }
   }
-  c->d = c->method == LT_MPDO ? 4 : 2;
+  c->d = c->method == LT_MPDO || c->method == LT_PURIFIED ? 4 : 2;
   c->slot = c->d * c->chi * c->chi;
   c->celt = c->prec == LT_MIXED ? sizeof(float2) : sizeof(double2);
   lt_status st = LT_OK;
@@ -451,6 +478,8 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   c->env_grid = env_grid(c);
   c->env_scratch_stride = c->method == LT_MPDO
                               ? (long long)(mpdo_scratch_bytes(L, c->chi) / c->celt)
+                          : c->method == LT_PURIFIED
+                              ? (long long)(purified_scratch_bytes(L, c->chi) / c->celt)
                               : (long long)env_scratch_elems(L, c->chi);
   if (st == LT_OK) st = dalloc(c, (char**)&c->B, nt * L * c->slot * c->celt);
   if (st == LT_OK) st = dalloc(c, &c->lam, nt * nb * c->chi);
@@ -585,6 +614,17 @@ lt_status lt_apply_noise(lt_ctx c, int64_t step) {
   return LT_OK;
 }
 
+lt_status lt_apply_kraus(lt_ctx c) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (c->method != LT_PURIFIED) {
+    c->last_error = "the R step belongs to the purified density matrix";
+    return LT_ERR_UNSUPPORTED;
+  }
+  LT_CK(launch_kraus(c));
+  return LT_OK;
+}
+
 lt_status lt_get_log_weights(lt_ctx c, double* out) {
   lt_status st = guard(c);
   if (st != LT_OK) return st;
@@ -614,6 +654,10 @@ lt_status lt_step(lt_ctx c, int32_t n_steps) {
       st = lt_apply_noise(c, c->step_counter);
       if (st != LT_OK) return st;
     }
+    if (c->method == LT_PURIFIED) {
+      st = lt_apply_kraus(c);
+      if (st != LT_OK) return st;
+    }
     c->step_counter++;
   }
   return LT_OK;
@@ -623,6 +667,7 @@ lt_status lt_measure_density(lt_ctx c, double* mean, double* sem, double* per_tr
   lt_status st = guard(c);
   if (st != LT_OK) return st;
   if (c->method == LT_MPDO) LT_CK(launch_mpdo_trace(c, false));
+  else if (c->method == LT_PURIFIED) LT_CK(launch_purified_env(c, false));
   else LT_CK(launch_env(c, 0, 0, nullptr));
   LT_CK(launch_reduce_density(c, c->red, c->red + c->L));
   if (mean) LT_CK(cudaMemcpyAsync(mean, c->red, sizeof(double) * c->L, cudaMemcpyDeviceToHost, c->stream));
@@ -642,6 +687,7 @@ lt_status lt_measure_corr(lt_ctx c, double* C_re, double* C_im, double* per_re, 
     if (st != LT_OK) return st;
   }
   if (c->method == LT_MPDO) LT_CK(launch_mpdo_trace(c, true));
+  else if (c->method == LT_PURIFIED) LT_CK(launch_purified_env(c, true));
   else LT_CK(launch_corr(c));
   LT_CK(launch_reduce_corr(c, c->red));
   std::vector<double> m(2 * LL);

@@ -195,7 +195,7 @@ struct MpdoArgs {
 // ---- context -------------------------------------------------------------------------
 struct lt_ctx_s {
   int L, chi, n_traj, prec, order, fermionic, max_sweeps, method;
-  int d;            // physical values per site: 2 (pure states), 4 (vectorised rho)
+  int d;            // values per site: 2 (pure states), 4 (vectorised rho; purified X, s = 2n + k)
   double J, dt, cut, jacobi_tol;
   uint64_t seed;
   long long traj_offset;
@@ -261,6 +261,9 @@ cudaError_t launch_qsd_noise(lt_ctx_s* c, long long step);
 cudaError_t launch_corr(lt_ctx_s* c);
 cudaError_t launch_mpdo_trace(lt_ctx_s* c, bool corr);
 size_t mpdo_scratch_bytes(int L, int chi);
+cudaError_t launch_kraus(lt_ctx_s* c);
+cudaError_t launch_purified_env(lt_ctx_s* c, bool corr);
+size_t purified_scratch_bytes(int L, int chi);
 cudaError_t launch_reduce_density(lt_ctx_s* c, double* out_mean, double* out_sem);
 cudaError_t launch_reduce_corr(lt_ctx_s* c, double* out);
 cudaError_t launch_convert_in(lt_ctx_s* c, const double* src, long long n, long long dst_off);

@@ -26,6 +26,9 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+template <typename R> struct MinNormal;
+template <> struct MinNormal<float> { static constexpr float v = FLT_MIN; };
+template <> struct MinNormal<double> { static constexpr double v = DBL_MIN; };
 template <typename R> struct Eps;
 template <> struct Eps<float> { static constexpr float v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
@@ -242,7 +245,10 @@ template <typename R>
 __device__ __forceinline__ bool rot_params(R gx, R gy, R alpha, R beta, R tol, R& cs, R& sex,
                                            R& sey, R& tga) {
   const R g2 = gx * gx + gy * gy;
-  if (!(alpha > (R)0 && beta > (R)0 && g2 > tol * tol * alpha * beta)) return false;
+  // below the normal range |g|^2 carries too few bits for 1/|g| (the rotation
+  // would not be unitary); such a pair is orthogonal to 1e-19 absolutely
+  if (!(alpha > (R)0 && beta > (R)0 && g2 > tol * tol * alpha * beta && g2 >= MinNormal<R>::v))
+    return false;
   const R inv = rsqrt_nr(g2);
   const R zeta = (beta - alpha) * (R)0.5 * inv;
   const R t = tangent(zeta, fabs(zeta));
@@ -594,6 +600,27 @@ template <> struct TinyNorm<double> { static constexpr double v = 1e-150; };
 // are replaced by (-ph alpha, 0, ...), and beta = 2/|e|^2 is returned (0 when
 // alpha is below TinyNorm, in which case the entries are simply set to zero:
 // they are below any precision of the result).  One warp.
+// The unit phase x0 / |x0| and |x0| of a reflector's leading entry.  x0 is scaled by
+// max(|Re x0|, |Im x0|) before it is squared: on a rank-deficient theta single
+// precision meets leading entries near 1e-23, whose square is subnormal, and a
+// phase taken from that rounded square is not of modulus one, which makes the
+// reflector non-unitary.
+template <typename R>
+__device__ __forceinline__ void unit_phase(R xr, R xi, R& phr, R& phi, R& ax) {
+  const R m = fmax(fabs(xr), fabs(xi));
+  if (!(m > (R)0)) {
+    phr = (R)1;
+    phi = (R)0;
+    ax = (R)0;
+    return;
+  }
+  const R sr = xr / m, si = xi / m;
+  const R nn = sqrt(sr * sr + si * si);
+  phr = sr / nn;
+  phi = si / nn;
+  ax = m * nn;
+}
+
 template <typename R>
 __device__ __forceinline__ R make_reflector(R* Xr, R* Xi, int base, int st, int len,
                                             typename CT<R>::T* dst) {
@@ -606,9 +633,10 @@ __device__ __forceinline__ R make_reflector(R* Xr, R* Xi, int base, int st, int 
   }
   warp_sum2(a2, dummy);
   const R x0r = Xr[base], x0i = Xi[base];
-  const R alpha = sqrt(a2), ax0 = sqrt(x0r * x0r + x0i * x0i);
+  const R alpha = sqrt(a2);
   const bool tiny = !(alpha > TinyNorm<R>::v);
-  const R phr = ax0 > (R)0 ? x0r / ax0 : (R)1, phi = ax0 > (R)0 ? x0i / ax0 : (R)0;
+  R phr, phi, ax0;
+  unit_phase(x0r, x0i, phr, phi, ax0);
   for (int t = lane; t < len; t += 32) {
     Tc e = cmk<Tc>(Xr[base + t * st], Xi[base + t * st]);
     if (t == 0) {
@@ -869,16 +897,10 @@ __device__ __forceinline__ void lq_build(const LQRow<G>& x, float* ebr, float* e
     const int p = (jn % G) * PART + jn / G;
     const float x0r = ebr[p], x0i = ebi[p];
     // square roots from the refined reciprocal square root (about one ulp)
-    const float n0 = x0r * x0r + x0i * x0i;
     const float alpha = a2 > 0.f ? a2 * rsqrt_nr(a2) : 0.f;
     const bool tiny = !(alpha > TinyNorm<float>::v);
-    float phr = 1.f, phi = 0.f, ax0 = 0.f;
-    if (n0 > 0.f) {
-      const float inv0 = rsqrt_nr(n0);
-      phr = x0r * inv0;
-      phi = x0i * inv0;
-      ax0 = n0 * inv0;
-    }
+    float phr, phi, ax0;
+    unit_phase(x0r, x0i, phr, phi, ax0);
     ebr[p] = x0r + phr * alpha;
     ebi[p] = x0i + phi * alpha;
     *bt_out = tiny ? 0.f : __frcp_rn(alpha * (alpha + ax0));
@@ -2178,6 +2200,362 @@ __global__ void __launch_bounds__(LT_BLOCK) mpdo_trace_kernel(MpdoArgs a) {
   }
 }
 
+// ---- locally purified density matrix (Sec. 3.2) ------------------------------------------
+// rho = X X^+ with X an MPS over s = 2n + k (physical n, Kraus k, chi_k = 2).
+__device__ __forceinline__ double2 d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 d2(double2 v) { return v; }
+
+// C (+)= sgn op(A) op(B) with double accumulation; op = identity or, with the h
+// flag, the conjugate transpose.  A and B are site-tensor slices (float2 or
+// double2) or double2 environments.
+template <typename TA, typename TB>
+__device__ void zgemm(int M, int N, int K, const TA* A, int lda, bool hA, const TB* B, int ldb,
+                      bool hB, double2* C, int ldc, bool acc, double sgn) {
+  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    double2 sacc = make_double2(0.0, 0.0);
+    for (int k = 0; k < K; ++k) {
+      double2 x = d2(hA ? A[(long long)k * lda + i] : A[(long long)i * lda + k]);
+      double2 y = d2(hB ? B[(long long)j * ldb + k] : B[(long long)k * ldb + j]);
+      if (hA) x.y = -x.y;
+      if (hB) y.y = -y.y;
+      sacc.x = fma(x.x, y.x, fma(-x.y, y.y, sacc.x));
+      sacc.y = fma(x.x, y.y, fma(x.y, y.x, sacc.y));
+    }
+    double2 o = acc ? C[(long long)i * ldc + j] : make_double2(0.0, 0.0);
+    o.x += sgn * sacc.x;
+    o.y += sgn * sacc.y;
+    C[(long long)i * ldc + j] = o;
+  }
+}
+
+// sum_{a,c} conj(P[a][c]) Q[a][c] over a (M x N) block of double2 P and slice Q
+template <typename TQ>
+__device__ double2 zdot(int M, int N, const TQ* P, int ldp, const double2* Qd, int ldq, double2* red) {
+  double2 part = make_double2(0.0, 0.0);
+  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    const double2 x = d2(P[(long long)i * ldp + j]), y = Qd[(long long)i * ldq + j];
+    part.x = fma(x.x, y.x, fma(x.y, y.y, part.x));
+    part.y = fma(x.x, y.y, fma(-x.y, y.x, part.y));
+  }
+  return block_sum_c2(part, red);
+}
+
+// The R step of one site (Eqs. MatrixR, NewPurified): the enlarged Kraus set
+// A~ = [A^{.,k} ; sqrt(gamma_c dt) L_c A^{.,k}] (identity first, then loss,
+// gain, dephasing with gamma > 0; columns p 2 + k), its Lambda_{i-1}-weighted
+// Gram matrix G = A~^+ W^2 A~ (at most 8 x 8), the two leading eigenvectors
+// V of G, and A <- A~ V.  G comes from the 16 n-resolved sums
+// g[m][m'][k][k'] = sum_{a,c} w_a^2 conj(B[a][2m+k][c]) B[a][2m'+k'][c]:
+// G[(p,k),(q,k')] = sum_n sum_{m,m'} O_p[n][m] O_q[n][m'] g[m][m'][k][k'].
+// One thread diagonalises G by cyclic complex Jacobi rotations in double.
+struct KrausArgs {
+  void* B;
+  const double* lam;
+  const int* dims;
+  int L, chi, slot, n_traj;
+  const double* gam;  // [3][L] loss, gain, dephasing
+  double dt;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(LT_BLOCK) kraus_step_kernel(KrausArgs a) {
+  typedef typename CT<R>::T Tc;
+  __shared__ double s_part[LT_BLOCK / 32][32];
+  __shared__ double s_g[32];
+  __shared__ double2 s_V[8][2];
+  __shared__ double s_op[4][4];  // op p: O_p[n][m] (real), row-major 2 x 2
+  __shared__ int s_nops;
+  const int L = a.L, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long ntask = (long long)a.n_traj * L;
+  for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
+    const int t = (int)(task / L), i = (int)(task - (long long)t * L);
+    const int* dm = a.dims + (long long)t * (L - 1);
+    const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+    Tc* Bi = reinterpret_cast<Tc*>(a.B) + ((long long)t * L + i) * a.slot;
+    const double* lw = a.lam + ((long long)t * (L - 1) + (i > 0 ? i - 1 : 0)) * a.chi;
+    if (tid == 0) {
+      int p = 0;
+      s_op[0][0] = 1.0; s_op[0][1] = 0.0; s_op[0][2] = 0.0; s_op[0][3] = 1.0;
+      const double g[3] = {a.gam[i], a.gam[L + i], a.gam[2 * L + i]};
+      for (int kind = 0; kind < 3; ++kind) {
+        if (!(g[kind] > 0.0)) continue;
+        const double r = sqrt(g[kind] * a.dt);
+        ++p;
+        for (int e = 0; e < 4; ++e) s_op[p][e] = 0.0;
+        if (kind == 0) s_op[p][0 * 2 + 1] = r;       // sigma- = |0><1|
+        else if (kind == 1) s_op[p][1 * 2 + 0] = r;  // sigma+ = |1><0|
+        else s_op[p][1 * 2 + 1] = r;                 // n
+      }
+      s_nops = p + 1;
+    }
+    // the 16 weighted sums g[m][m'][k][k'] (complex: 32 doubles per thread)
+    double acc[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) acc[e] = 0.0;
+    for (int x = tid; x < cl * cr; x += blockDim.x) {
+      const int aa = x / cr, c = x - aa * cr;
+      const double w = i > 0 ? lw[aa] : 1.0, w2 = w * w;
+      double2 v[4];
+#pragma unroll
+      for (int sidx = 0; sidx < 4; ++sidx) v[sidx] = d2(Bi[(long long)(aa * 4 + sidx) * cr + c]);
+#pragma unroll
+      for (int s1 = 0; s1 < 4; ++s1)
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+          // conj(v[s1]) v[s2], s = 2m + k: index ((m1 2 + m2) 2 + k1) 2 + k2
+          const int m1 = s1 >> 1, k1 = s1 & 1, m2 = s2 >> 1, k2 = s2 & 1;
+          const int e = (((m1 * 2 + m2) * 2 + k1) * 2 + k2) * 2;
+          acc[e] = fma(w2, v[s1].x * v[s2].x + v[s1].y * v[s2].y, acc[e]);
+          acc[e + 1] = fma(w2, v[s1].x * v[s2].y - v[s1].y * v[s2].x, acc[e + 1]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      double v = acc[e];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      if (lane == 0) s_part[warp][e] = v;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_part[w][tid];
+      s_g[tid] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int np = s_nops, nc = 2 * np;
+      double2 G[8][8], V[8][8];
+      for (int P = 0; P < nc; ++P)
+        for (int Q = 0; Q < nc; ++Q) {
+          const int p = P >> 1, k1 = P & 1, q = Q >> 1, k2 = Q & 1;
+          double2 z = make_double2(0.0, 0.0);
+          for (int n = 0; n < 2; ++n)
+            for (int m1 = 0; m1 < 2; ++m1)
+              for (int m2 = 0; m2 < 2; ++m2) {
+                const double o = s_op[p][n * 2 + m1] * s_op[q][n * 2 + m2];
+                if (o == 0.0) continue;
+                const int e = (((m1 * 2 + m2) * 2 + k1) * 2 + k2) * 2;
+                z.x += o * s_g[e];
+                z.y += o * s_g[e + 1];
+              }
+          G[P][Q] = z;
+          V[P][Q] = make_double2(P == Q ? 1.0 : 0.0, 0.0);
+        }
+      // cyclic Jacobi for the Hermitian G: for the pair (p, q) with
+      // G_pq = |b| e, the unitary U = D J (D = diag(1, conj e) on (p, q), J the
+      // real rotation that diagonalises D^+ G D) gives U^+ G U with G_pq = 0
+      double scale = 0.0;
+      for (int P = 0; P < nc; ++P) scale = fmax(scale, fabs(G[P][P].x));
+      for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0;
+        for (int P = 0; P < nc; ++P)
+          for (int Q = P + 1; Q < nc; ++Q) off = fmax(off, hypot(G[P][Q].x, G[P][Q].y));
+        if (!(off > 1e-15 * scale)) break;
+        for (int p = 0; p < nc; ++p)
+          for (int q = p + 1; q < nc; ++q) {
+            const double ab = hypot(G[p][q].x, G[p][q].y);
+            if (!(ab > 1e-300)) continue;
+            const double ex = G[p][q].x / ab, ey = G[p][q].y / ab;  // e
+            const double tau = (G[q][q].x - G[p][p].x) / (2.0 * ab);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = 1.0 / sqrt(1.0 + tt * tt), sn = tt * c;
+            // columns: new p = c col_p - s conj(e) col_q, new q = s col_p + c conj(e) col_q
+            for (int r = 0; r < nc; ++r) {
+              const double2 gp = G[r][p], gq = G[r][q];
+              const double2 qe = make_double2(gq.x * ex + gq.y * ey, gq.y * ex - gq.x * ey);  // gq conj(e)
+              G[r][p] = make_double2(c * gp.x - sn * qe.x, c * gp.y - sn * qe.y);
+              G[r][q] = make_double2(sn * gp.x + c * qe.x, sn * gp.y + c * qe.y);
+              const double2 vp = V[r][p], vq = V[r][q];
+              const double2 ve = make_double2(vq.x * ex + vq.y * ey, vq.y * ex - vq.x * ey);
+              V[r][p] = make_double2(c * vp.x - sn * ve.x, c * vp.y - sn * ve.y);
+              V[r][q] = make_double2(sn * vp.x + c * ve.x, sn * vp.y + c * ve.y);
+            }
+            // rows: new p = c row_p - s e row_q, new q = s row_p + c e row_q
+            for (int r = 0; r < nc; ++r) {
+              const double2 gp = G[p][r], gq = G[q][r];
+              const double2 qe = make_double2(gq.x * ex - gq.y * ey, gq.y * ex + gq.x * ey);  // e gq
+              G[p][r] = make_double2(c * gp.x - sn * qe.x, c * gp.y - sn * qe.y);
+              G[q][r] = make_double2(sn * gp.x + c * qe.x, sn * gp.y + c * qe.y);
+            }
+            G[p][q] = make_double2(0.0, 0.0);
+            G[q][p] = make_double2(0.0, 0.0);
+          }
+      }
+      // the two largest eigenvalues (ties to the lower index)
+      int first = 0;
+      for (int P = 1; P < nc; ++P)
+        if (G[P][P].x > G[first][first].x) first = P;
+      int second = first == 0 ? 1 : 0;
+      for (int P = 0; P < nc; ++P)
+        if (P != first && G[P][P].x > G[second][second].x) second = P;
+      for (int P = 0; P < 8; ++P) {
+        s_V[P][0] = P < nc ? V[P][first] : make_double2(0.0, 0.0);
+        s_V[P][1] = P < nc ? V[P][second] : make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+    // A <- A~ V: new B[a][2n + k][c] = sum_{p,k0} (O_p B_{k0})[a][n][c] V[p 2 + k0][k]
+    const int np = s_nops;
+    for (int x = tid; x < cl * cr; x += blockDim.x) {
+      const int aa = x / cr, c = x - aa * cr;
+      double2 v[4];
+#pragma unroll
+      for (int sidx = 0; sidx < 4; ++sidx) v[sidx] = d2(Bi[(long long)(aa * 4 + sidx) * cr + c]);
+      double2 o[4];
+#pragma unroll
+      for (int sidx = 0; sidx < 4; ++sidx) o[sidx] = make_double2(0.0, 0.0);
+      for (int p = 0; p < np; ++p)
+        for (int k0 = 0; k0 < 2; ++k0)
+          for (int n = 0; n < 2; ++n) {
+            double2 col = make_double2(0.0, 0.0);  // (O_p B_{k0})[a][n][c]
+            for (int m = 0; m < 2; ++m) {
+              const double op = s_op[p][n * 2 + m];
+              col.x += op * v[m * 2 + k0].x;
+              col.y += op * v[m * 2 + k0].y;
+            }
+            for (int k = 0; k < 2; ++k) {
+              const double2 w = s_V[p * 2 + k0][k];
+              o[n * 2 + k].x += col.x * w.x - col.y * w.y;
+              o[n * 2 + k].y += col.x * w.y + col.y * w.x;
+            }
+          }
+#pragma unroll
+      for (int sidx = 0; sidx < 4; ++sidx)
+        Bi[(long long)(aa * 4 + sidx) * cr + c] = cmk<Tc>(o[sidx].x, o[sidx].y);
+    }
+    __syncthreads();
+  }
+}
+
+// <n_i> and C_ij of rho = X X^+: <X| O (x) 1 |X> / <X|X> with exact environments in
+// double (one CTA per chain).  Lenv_{i+1} = sum_s B_s^+ Lenv_i B_s and
+// Renv_i = sum_s B_s Renv_{i+1} B_s^+ over the four values s = 2n + k;
+// <n_i> <X|X> = sum_{k} <B_{(1,k)}, Lenv_i B_{(1,k)} Renv_{i+1}>; for i < j
+// C_ij <X|X> = sum_k <B_j(0,k), E B_j(1,k) Renv_{j+1}> with
+// E = sum_k B_i(1,k)^+ Lenv_i B_i(0,k) carried through the sites between by
+// sum_k [B(0,k)^+ E B(0,k) - B(1,k)^+ E B(1,k)] (the string).
+struct PurEnvArgs {
+  const void* B;
+  const int* dims;
+  int L, chi, slot, n_traj;
+  double2* scratch;  // per CTA: Renv [L+1][chi^2], Lenv [L+1][chi^2], T, E, E2 [chi^2]
+  long long stride;
+  double* density;   // [n_traj][L]
+  double2* corr;     // [n_traj][L][L] or nullptr
+};
+
+template <typename R>
+__global__ void __launch_bounds__(LT_BLOCK) purified_env_kernel(PurEnvArgs a) {
+  typedef typename CT<R>::T Tc;
+  __shared__ double2 s_red[LT_BLOCK / 32];
+  const int L = a.L, chi = a.chi, tid = threadIdx.x;
+  const long long chi2 = (long long)chi * chi;
+  double2* Renv = a.scratch + (long long)blockIdx.x * a.stride;
+  double2* Lenv = Renv + (long long)(L + 1) * chi2;
+  double2* T = Lenv + (long long)(L + 1) * chi2;
+  double2* E = T + chi2;
+  double2* E2 = E + chi2;
+  for (int t = blockIdx.x; t < a.n_traj; t += gridDim.x) {
+    const int* dm = a.dims + (long long)t * (L - 1);
+    const Tc* Bt = reinterpret_cast<const Tc*>(a.B) + (long long)t * L * a.slot;
+    if (tid == 0) {
+      Renv[(long long)L * chi2] = make_double2(1.0, 0.0);
+      Lenv[0] = make_double2(1.0, 0.0);
+    }
+    __syncthreads();
+    for (int i = L - 1; i >= 0; --i) {
+      const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+      const Tc* Bi = Bt + (long long)i * a.slot;
+      for (int s = 0; s < 4; ++s) {
+        zgemm(cl, cr, cr, Bi + s * cr, 4 * cr, false, Renv + (long long)(i + 1) * chi2, chi, false,
+              T, chi, false, 1.0);
+        __syncthreads();
+        zgemm(cl, cl, cr, T, chi, false, Bi + s * cr, 4 * cr, true, Renv + (long long)i * chi2, chi,
+              s > 0, 1.0);
+        __syncthreads();
+      }
+    }
+    const double nrm = Renv[0].x;
+    for (int i = 0; i < L; ++i) {
+      const int cl = i == 0 ? 1 : dm[i - 1], cr = i == L - 1 ? 1 : dm[i];
+      const Tc* Bi = Bt + (long long)i * a.slot;
+      double2 num = make_double2(0.0, 0.0);
+      for (int k = 0; k < 2; ++k) {
+        const Tc* B1 = Bi + (2 + k) * cr;
+        zgemm(cl, cr, cl, Lenv + (long long)i * chi2, chi, false, B1, 4 * cr, false, T, chi, false, 1.0);
+        __syncthreads();
+        zgemm(cl, cr, cr, T, chi, false, Renv + (long long)(i + 1) * chi2, chi, false, E, chi, false, 1.0);
+        __syncthreads();
+        const double2 d = zdot(cl, cr, B1, 4 * cr, E, chi, s_red);
+        num.x += d.x;
+        num.y += d.y;
+      }
+      if (tid == 0) {
+        a.density[(long long)t * L + i] = num.x / nrm;
+        if (a.corr) a.corr[((long long)t * L + i) * L + i] = make_double2(num.x / nrm, 0.0);
+      }
+      for (int s = 0; s < 4; ++s) {
+        zgemm(cl, cr, cl, Lenv + (long long)i * chi2, chi, false, Bi + s * cr, 4 * cr, false, T, chi,
+              false, 1.0);
+        __syncthreads();
+        zgemm(cr, cr, cl, Bi + s * cr, 4 * cr, true, T, chi, false, Lenv + (long long)(i + 1) * chi2,
+              chi, s > 0, 1.0);
+        __syncthreads();
+      }
+    }
+    if (a.corr) {
+      for (int i = 0; i + 1 < L; ++i) {
+        const int cl = i == 0 ? 1 : dm[i - 1], cr = dm[i];
+        const Tc* Bi = Bt + (long long)i * a.slot;
+        for (int k = 0; k < 2; ++k) {  // E = sum_k B(1,k)^+ Lenv_i B(0,k)
+          zgemm(cl, cr, cl, Lenv + (long long)i * chi2, chi, false, Bi + k * cr, 4 * cr, false, T, chi,
+                false, 1.0);
+          __syncthreads();
+          zgemm(cr, cr, cl, Bi + (2 + k) * cr, 4 * cr, true, T, chi, false, E, chi, k > 0, 1.0);
+          __syncthreads();
+        }
+        for (int j = i + 1; j < L; ++j) {
+          const int jl = dm[j - 1], jr = j == L - 1 ? 1 : dm[j];
+          const Tc* Bj = Bt + (long long)j * a.slot;
+          double2 num = make_double2(0.0, 0.0);
+          for (int k = 0; k < 2; ++k) {
+            zgemm(jl, jr, jl, E, chi, false, Bj + (2 + k) * jr, 4 * jr, false, T, chi, false, 1.0);
+            __syncthreads();
+            zgemm(jl, jr, jr, T, chi, false, Renv + (long long)(j + 1) * chi2, chi, false, E2, chi,
+                  false, 1.0);
+            __syncthreads();
+            const double2 d = zdot(jl, jr, Bj + k * jr, 4 * jr, E2, chi, s_red);
+            num.x += d.x;
+            num.y += d.y;
+          }
+          if (tid == 0) {
+            a.corr[((long long)t * L + i) * L + j] = make_double2(num.x / nrm, num.y / nrm);
+            a.corr[((long long)t * L + j) * L + i] = make_double2(num.x / nrm, -num.y / nrm);
+          }
+          if (j + 1 < L) {  // E <- sum_k [B(0,k)^+ E B(0,k) - B(1,k)^+ E B(1,k)]
+            for (int s = 0; s < 4; ++s) {
+              zgemm(jl, jr, jl, E, chi, false, Bj + s * jr, 4 * jr, false, T, chi, false, 1.0);
+              __syncthreads();
+              zgemm(jr, jr, jl, Bj + s * jr, 4 * jr, true, T, chi, false, E2, chi, s > 0,
+                    s < 2 ? 1.0 : -1.0);
+              __syncthreads();
+            }
+            for (int x = tid; x < jr * jr; x += blockDim.x) {
+              const int r = x / jr, c = x - r * jr;
+              E[(long long)r * chi + c] = E2[(long long)r * chi + c];
+            }
+            __syncthreads();
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __global__ void convert_in_kernel(typename CT<R>::T* dst, const double* src, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -2197,17 +2575,18 @@ __global__ void convert_out_kernel(double* dst, const typename CT<R>::T* src, lo
 
 // Product state: |n_i> per site for pure states (d = 2); for the vectorised
 // density matrix (d = 4) the site factor |n_i><n_i| has the one non-zero local
-// index m = 2 n_i + n_i = 3 n_i (Eq. MPDO).
+// index m = 2 n_i + n_i = 3 n_i (Eq. MPDO); for the purified density matrix
+// X = |n> with Kraus index 0, s = 2 n_i.  occ_index is the index of n_i = 1.
 template <typename R>
 __global__ void init_state_kernel(typename CT<R>::T* B, double* lam, int* dims, double* trunc,
                                   int* evolve, int* channel, const uint8_t* occ, int n_traj,
-                                  int L, int chi, int slot, int d) {
+                                  int L, int chi, int slot, int d, int occ_index) {
   const long long nt = (long long)n_traj * L;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt;
        i += (long long)gridDim.x * blockDim.x) {
     const int traj = (int)(i / L), site = (int)(i - (long long)traj * L);
     typename CT<R>::T* s = B + i * slot;
-    const int on = occ[site] ? d - 1 : 0;
+    const int on = occ[site] ? occ_index : 0;
     for (int m = 0; m < d; ++m) s[m] = cmk<typename CT<R>::T>(m == on ? 1.0 : 0.0, 0.0);
     if (site < L - 1) {
       const long long bi = (long long)traj * (L - 1) + site;
@@ -2306,7 +2685,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.tol = c->jacobi_tol;
   a.sweep_hist = c->sweep_hist;
   a.counters = c->counters;
-  a.keep_norm = c->method == LT_QSD && mode == 0;
+  a.keep_norm = (c->method == LT_QSD || c->method == LT_PURIFIED) && mode == 0;
   a.logw = c->method == LT_QSD && mode == 2 ? c->logw : nullptr;
   a.multiplet = c->method == LT_MPDO ? (c->prec == LT_MIXED ? 1e-5 : 1e-9) : 0.0;
   bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0,
@@ -2393,6 +2772,47 @@ cudaError_t launch_mpdo_trace(lt_ctx_s* c, bool corr) {
   return cudaGetLastError();
 }
 
+size_t purified_scratch_bytes(int L, int chi) {
+  return (2 * (size_t)L + 5) * (size_t)chi * chi * sizeof(double2);
+}
+
+cudaError_t launch_kraus(lt_ctx_s* c) {
+  KrausArgs a;
+  a.B = c->B;
+  a.lam = c->lam;
+  a.dims = c->dims;
+  a.L = c->L;
+  a.chi = c->chi;
+  a.slot = c->slot;
+  a.n_traj = c->n_traj;
+  a.gam = c->gam;
+  a.dt = c->dt;
+  const long long ntask = (long long)c->n_traj * c->L;
+  const int grid = (int)(ntask < 8LL * c->num_sms ? ntask : 8LL * c->num_sms);
+  if (c->prec == LT_MIXED) kraus_step_kernel<float><<<grid, LT_BLOCK, 0, c->stream>>>(a);
+  else kraus_step_kernel<double><<<grid, LT_BLOCK, 0, c->stream>>>(a);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_purified_env(lt_ctx_s* c, bool corr) {
+  PurEnvArgs a;
+  a.B = c->B;
+  a.dims = c->dims;
+  a.L = c->L;
+  a.chi = c->chi;
+  a.slot = c->slot;
+  a.n_traj = c->n_traj;
+  a.scratch = reinterpret_cast<double2*>(c->env_scratch);
+  a.stride = (long long)(c->env_scratch_stride * c->celt / sizeof(double2));
+  a.density = c->density;
+  a.corr = corr ? c->corr : nullptr;
+  if (c->prec == LT_MIXED) purified_env_kernel<float><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
+  else purified_env_kernel<double><<<c->env_grid, LT_BLOCK, 0, c->stream>>>(a);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_jump_apply(lt_ctx_s* c) {
   const int grid = c->n_traj < 4 * c->num_sms ? c->n_traj : 4 * c->num_sms;
   if (c->prec == LT_MIXED)
@@ -2468,14 +2888,15 @@ cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long 
 
 cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev) {
   const long long nt = (long long)c->n_traj * c->L;
+  const int occ_index = c->d == 2 ? 1 : (c->method == LT_MPDO ? 3 : 2);
   if (c->prec == LT_MIXED)
     init_state_kernel<float><<<grid_for(nt, 256), 256, 0, c->stream>>>(
         reinterpret_cast<float2*>(c->B), c->lam, c->dims, c->trunc, c->evolve, c->channel, occ_dev,
-        c->n_traj, c->L, c->chi, c->slot, c->d);
+        c->n_traj, c->L, c->chi, c->slot, c->d, occ_index);
   else
     init_state_kernel<double><<<grid_for(nt, 256), 256, 0, c->stream>>>(
         reinterpret_cast<double2*>(c->B), c->lam, c->dims, c->trunc, c->evolve, c->channel, occ_dev,
-        c->n_traj, c->L, c->chi, c->slot, c->d);
+        c->n_traj, c->L, c->chi, c->slot, c->d, occ_index);
   c->launches++;
   return cudaGetLastError();
 }

@@ -63,7 +63,7 @@ namespace {
 uint64_t context_bytes(const lt_config* cfg, int num_sms) {
   const uint64_t L = cfg->L, chi = cfg->chi_max, nt = cfg->n_traj, nb = L - 1;
   const uint64_t celt = cfg->precision == LT_MIXED ? 8 : 16;
-  const uint64_t d = cfg->method == LT_MPDO ? 4 : 2;
+  const uint64_t d = cfg->method == LT_MPDO || cfg->method == LT_PURIFIED ? 4 : 2;
   const uint64_t slot = d * chi * chi;
   uint64_t b = nt * L * slot * celt;                       // site tensors
   b += nt * nb * chi * 8 + nt * nb * 4 + nt * nb * 8;      // Lambda, dims, truncation
@@ -76,8 +76,9 @@ uint64_t context_bytes(const lt_config* cfg, int num_sms) {
   uint64_t env_grid = nt < 8ull * num_sms ? nt : 8ull * num_sms;
   const uint64_t cap = (uint64_t)env_grid_cap((int)L, (int)chi, celt, num_sms);
   if (env_grid > cap) env_grid = cap;
-  b += env_grid * (d == 4 ? (uint64_t)mpdo_scratch_bytes((int)L, (int)chi)
-                          : env_scratch_elems((int)L, (int)chi) * celt);
+  b += env_grid * (cfg->method == LT_MPDO       ? (uint64_t)mpdo_scratch_bytes((int)L, (int)chi)
+                   : cfg->method == LT_PURIFIED ? (uint64_t)purified_scratch_bytes((int)L, (int)chi)
+                                                : env_scratch_elems((int)L, (int)chi) * celt);
   return b;
 }
 

@@ -37,7 +37,7 @@ class lt_config(ctypes.Structure):
 
 
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
-           "lt_get_log_weights",
+           "lt_apply_kraus", "lt_get_log_weights",
            "lt_step", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
@@ -56,6 +56,7 @@ def load_library(path=LIB_PATH):
         "lt_apply_layer": ([P, I32, D], I32),
         "lt_apply_jumps": ([P, I64, P, P], I32),
         "lt_apply_noise": ([P, I64], I32),
+        "lt_apply_kraus": ([P], I32),
         "lt_get_log_weights": ([P, P], I32),
         "lt_step": ([P, I32], I32),
         "lt_measure_density": ([P, P, P, P], I32),
@@ -121,11 +122,11 @@ def _arr(x, L, dtype=np.float64):
 def make_config(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.05,
                 trotter_order=2, gamma_loss=None, gamma_gain=None, gamma_deph=None,
                 fermionic_jumps=1, svd_cut=1e-12, seed=0, traj_offset=0, product_occ=None,
-                method=LT_TRAJ, max_sweeps=0, jacobi_tol=0.0):
+                method=LT_TRAJ, max_sweeps=0, jacobi_tol=0.0, kraus_dim=0):
     """An lt_config and the arrays it points to (keep both alive while it is used)."""
     cfg = lt_config()
     cfg.L, cfg.chi_max, cfg.n_traj = L, chi_max, n_traj
-    cfg.kraus_dim, cfg.method, cfg.precision = 0, method, precision
+    cfg.kraus_dim, cfg.method, cfg.precision = kraus_dim, method, precision
     cfg.init = INIT_NAMES[init] if isinstance(init, str) else int(init)
     cfg.trotter_order, cfg.J, cfg.dt = trotter_order, J, dt
     keep = [_arr(gamma_loss, L), _arr(gamma_gain, L), _arr(gamma_deph, L),
@@ -165,6 +166,10 @@ def lt_apply_jumps(ctx, step, replay=None, n_traj=None, want_channels=False):
 
 def lt_apply_noise(ctx, step):
     _check(_lib.lt_apply_noise(ctx, step), "lt_apply_noise", ctx)
+
+
+def lt_apply_kraus(ctx):
+    _check(_lib.lt_apply_kraus(ctx), "lt_apply_kraus", ctx)
 
 
 def lt_get_log_weights(ctx, n_traj):
@@ -292,7 +297,7 @@ class Ensemble:
 
     def __init__(self, L, chi_max, n_traj, **kw):
         self.L, self.chi, self.n_traj = L, chi_max, n_traj
-        self.d = 4 if kw.get("method", LT_TRAJ) == LT_MPDO else 2
+        self.d = 4 if kw.get("method", LT_TRAJ) in (LT_MPDO, LT_PURIFIED) else 2
         self.ctx = lt_create(L, chi_max, n_traj, **kw)
 
     def close(self):
@@ -323,6 +328,9 @@ class Ensemble:
 
     def apply_noise(self, step):
         lt_apply_noise(self.ctx, step)
+
+    def apply_kraus(self):
+        lt_apply_kraus(self.ctx)
 
     def log_weights(self):
         return lt_get_log_weights(self.ctx, self.n_traj)

@@ -1,0 +1,125 @@
+"""GPU parity of the locally purified density matrix (Sec. 3.2) through the C ABI
+against the FP64 oracle: rho = X X^+ with X an MPS over s = 2n + k (Kraus
+dimension 2), effective-Hamiltonian layers that keep the norm, then the R step
+on every site (Eqs. MatrixR, NewPurified).  Per chain <n_i> and C_ij within 1e-10
+in FP64 and within the single-precision bound below in mixed precision.  The
+R step keeps two eigenvectors; the rates are chosen unequal so that no two
+eigenvalues tie at that cut (a tie makes the kept Kraus vector arbitrary)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import purified, tebd
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 5e-5
+
+
+def _lt():
+    from paper_2609_18841_b300 import lindtebd
+    return lindtebd
+
+
+def cfg_of(L, chi, dt=0.05, loss=0.0, gain=0.0, deph=0.0, fermionic=False, occ="neel",
+           cut=1e-12):
+    return tebd.TrajectoryConfig(L, J=1.0, dt=dt, chi_max=chi, svd_cut=cut, gamma_loss=loss,
+                                 gamma_gain=gain, gamma_deph=deph, fermionic=fermionic,
+                                 occupation=workloads.occupation(L, occ))
+
+
+def source_sink(L, chi, g=0.6, deph=0.13, dt=0.05):
+    loss = np.zeros(L)
+    gain = np.zeros(L)
+    gain[0], loss[-1] = g, 0.9 * g
+    return cfg_of(L, chi, dt=dt, loss=loss, gain=gain, deph=deph, fermionic=True, occ="vacuum")
+
+
+def ensemble(cfg, n, precision, cut=None):
+    lt = _lt()
+    return lt.Ensemble(cfg.L, cfg.chi_max, n, method=lt.LT_PURIFIED, kraus_dim=2,
+                       precision=precision, init="product",
+                       product_occ=cfg.occupation.astype(np.uint8), J=cfg.J, dt=cfg.dt,
+                       gamma_loss=cfg.gamma_loss, gamma_gain=cfg.gamma_gain,
+                       gamma_deph=cfg.gamma_deph, fermionic_jumps=int(cfg.fermionic),
+                       svd_cut=cfg.svd_cut if cut is None else cut)
+
+
+def close(got, want, tol, what):
+    scale = max(1.0, float(np.abs(want).max()))
+    err = float(np.abs(got - want).max())
+    assert err <= tol * scale, "%s: max |diff| %.3e > %.1e" % (what, err, tol * scale)
+    return err
+
+
+CASES = [
+    ("source_sink_chi16", lambda: source_sink(8, 16), 10),
+    ("loss_gain_deph_chi32", lambda: cfg_of(9, 32, loss=0.1, gain=0.05, deph=0.07), 8),
+    ("loss_gain_chi64", lambda: cfg_of(8, 64, dt=0.1, loss=0.3, gain=0.2, deph=0.11), 6),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def case(request):
+    name, make, steps = request.param
+    cfg = make()
+    return cfg, steps, purified.run_purified(cfg, 2, steps, measure_corr=True)
+
+
+def test_purified_fp64_matches_the_oracle(case):
+    cfg, steps, res = case
+    lt = _lt()
+    with ensemble(cfg, 2, lt.LT_FP64) as e:
+        e.step(steps)
+        _, sem, per = e.density(per_traj=True)
+        _, Cp = e.corr(per_traj=True)
+        tw, dims = e.stats()
+    for t in range(2):
+        close(per[t], res["density"], FP64_TOL, "density")
+        close(Cp[t], res["corr"], FP64_TOL, "correlation")
+        assert list(dims[t]) == list(res["bond_dims"])
+    assert np.all(sem < 1e-12)
+
+
+def test_purified_mixed_precision(case):
+    cfg, steps, res = case
+    lt = _lt()
+    with ensemble(cfg, 1, lt.LT_MIXED, cut=1e-6) as e:
+        e.step(steps)
+        _, _, per = e.density(per_traj=True)
+        _, Cp = e.corr(per_traj=True)
+    close(per[0], res["density"], MIXED_TOL, "mixed density")
+    close(Cp[0], res["corr"], MIXED_TOL, "mixed correlation")
+
+
+def test_step_equals_layers_then_r_step():
+    lt = _lt()
+    cfg = cfg_of(7, 16, loss=0.2, gain=0.1, deph=0.05)
+    with ensemble(cfg, 1, lt.LT_FP64) as a, ensemble(cfg, 1, lt.LT_FP64) as b:
+        a.step(4)
+        for _ in range(4):
+            for parity, tau in cfg.layers():
+                b.apply_layer(parity, tau)
+            b.apply_kraus()
+        assert np.array_equal(a.density(per_traj=True)[2], b.density(per_traj=True)[2])
+    with lt.Ensemble(6, 8, 1, precision=lt.LT_FP64, gamma_loss=0.1) as t:
+        with pytest.raises(lt.LtError) as err:
+            t.apply_kraus()
+        assert err.value.status == lt.LT_ERR_UNSUPPORTED
+
+
+def test_chain_of_64_sites_sampled():
+    # 64 sites, spin loss, gain and dephasing on every site, chi_max = 64,
+    # the first steps through the oracle site by site
+    lt = _lt()
+    cfg = cfg_of(64, 64, dt=0.02, loss=0.1, gain=0.05, deph=0.03)
+    steps = 3
+    res = purified.run_purified(cfg, 2, steps, measure_corr=True)
+    for prec, tol, cut in ((lt.LT_FP64, FP64_TOL, 1e-12), (lt.LT_MIXED, MIXED_TOL, 1e-6)):
+        with ensemble(cfg, 1, prec, cut=cut) as e:
+            e.step(steps)
+            _, _, per = e.density(per_traj=True)
+            _, Cp = e.corr(per_traj=True)
+        close(per[0], res["density"], tol, "density")
+        close(Cp[0], res["corr"], tol, "corr")
