@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--mpdo-sat-steps", type=int, default=3)
     ap.add_argument("--mpdo-acc-steps", type=int, default=20)
     ap.add_argument("--mpdo-batch", type=int, default=148)
+    ap.add_argument("--purified-steps", type=int, default=50)
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
@@ -202,28 +203,103 @@ def random_mpdo(L, chi, seed):
     return B, lam, dims
 
 
-def mpdo_cpu_oracle(seconds, L, chi, kw):
-    """The FP64 MPDO oracle as it stands: Trotter layers on the saturated
+def dm_cpu_oracle(seconds, method_name, L, chi, rates, init):
+    """The FP64 oracle of a density-matrix method as it stands: time steps (the
+    Trotter layers, and for the purified form the R step) on the saturated
     synthetic chain until about `seconds` of CPU work."""
-    from oracle import mpdo, tebd
-    cfg = tebd.TrajectoryConfig(L, J=1.0, dt=kw["dt"], chi_max=chi, svd_cut=1e-12,
-                                gamma_loss=kw["gamma_loss"], gamma_gain=kw["gamma_gain"],
-                                fermionic=False, occupation=workloads.occupation(L, "domain_wall"))
+    from oracle import mpdo, purified, tebd
+    cfg = tebd.TrajectoryConfig(L, J=1.0, dt=rates["dt"], chi_max=chi, svd_cut=1e-12,
+                                gamma_loss=rates.get("gamma_loss", 0.0),
+                                gamma_gain=rates.get("gamma_gain", 0.0),
+                                gamma_deph=rates.get("gamma_deph", 0.0), fermionic=False,
+                                occupation=workloads.occupation(L, init))
     B, lam, _ = random_mpdo(L, chi, 99)
-    m = mpdo.MPDO(cfg)
+    if method_name == "mpdo":
+        m = mpdo.MPDO(cfg)
+        gates = {tau: mpdo.bond_gates(cfg, tau) for _, tau in cfg.layers()}
+    else:
+        m = purified.Purified(cfg, 2)
+        gates = {tau: [purified.full_gate(G, 2) for G in cfg.gates(tau)] for _, tau in cfg.layers()}
     m.B, m.lam = [b.copy() for b in B], [x.copy() for x in lam]
-    gates = {tau: mpdo.bond_gates(cfg, tau) for _, tau in cfg.layers()}
-    updates, layers = 0, 0
+    updates, steps = 0, 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds:
         for parity, tau in cfg.layers():
             m.apply_layer(parity, gates[tau])
             updates += len(range(parity, L - 1, 2))
-            layers += 1
+        if method_name == "purified":
+            m.kraus_steps()
+        steps += 1
     dt = time.perf_counter() - t0
     return {"value": updates / dt, "unit": "two-site updates/s", "kind": "oracle",
-            "sample": "%d Trotter layers (%d updates) of the saturated L=%d, chi=%d chain, "
-                      "%.1f s" % (layers, updates, L, chi, dt)}
+            "sample": "%d time steps (%d two-site updates) of the saturated L=%d, chi=%d chain, "
+                      "%.1f s" % (steps, updates, L, chi, dt)}
+
+
+def density_matrix_leg(lt, stream, args, alu_peak, method, L, chi, init, rates, steps, workload):
+    """Time to solution of one chain in mixed precision, the per-step cost of the
+    saturated chain in both precisions, mixed against FP64 over the first steps,
+    a batch of 148 chains at chi = 32 (theta 128 x 128), and the oracle."""
+    name = "mpdo" if method == lt.LT_MPDO else "purified"
+    kw = dict(method=method, init=init, fermionic_jumps=0, stream=stream.cuda_stream, **rates)
+    if method == lt.LT_PURIFIED:
+        kw["kraus_dim"] = 2
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(e, n):
+        torch.cuda.synchronize()
+        e.counters(clear=True)
+        ev[0].record(stream)
+        lt.lt_step(e.ctx, n)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3, e.counters()
+
+    with lt.Ensemble(L, chi, 1, precision=lt.LT_MIXED, svd_cut=1e-6, **kw) as e:
+        s_tts, c_tts = timed(e, steps)
+        n_end = e.density()[0]
+        _, dims_end = e.stats()
+    sat = {}
+    state = random_mpdo(L, chi, 99)
+    for pname, prec, cut, n in (("mixed", lt.LT_MIXED, 1e-6, args.mpdo_sat_steps),
+                                ("fp64", lt.LT_FP64, 1e-12, max(1, args.mpdo_sat_steps - 1))):
+        with lt.Ensemble(L, chi, 1, precision=prec, svd_cut=cut, **kw) as e:
+            e.set_state(0, [state])
+            s_sat, c_sat = timed(e, n)
+        tfl = c_sat["layer_flops"] / s_sat / 1e12
+        sat[pname] = {"steps": n, "ms_per_step": 1e3 * s_sat / n,
+                      "updates_per_s": c_sat["layer_updates"] / s_sat,
+                      "bond_kernel_tflops": tfl, "alu_frac": tfl / alu_peak}
+    acc = None
+    if args.mpdo_acc_steps > 0:
+        out = {}
+        for pname, prec, cut in (("mixed", lt.LT_MIXED, 1e-6), ("fp64", lt.LT_FP64, 1e-12)):
+            with lt.Ensemble(L, chi, 1, precision=prec, svd_cut=cut, **kw) as e:
+                e.step(args.mpdo_acc_steps)
+                out[pname] = (e.density()[0], e.corr()[0])
+        acc = {"steps": args.mpdo_acc_steps,
+               "max_abs_density": float(np.abs(out["mixed"][0] - out["fp64"][0]).max()),
+               "max_abs_corr": float(np.abs(out["mixed"][1] - out["fp64"][1]).max())}
+    batch = None
+    if args.mpdo_batch > 0:
+        nbt, Lb, chib = args.mpdo_batch, 24, 32
+        with lt.Ensemble(Lb, chib, nbt, precision=lt.LT_MIXED, svd_cut=1e-6, **kw) as e:
+            e.set_state(0, [random_mpdo(Lb, chib, 7)] * nbt)
+            lt.lt_step(e.ctx, 1)
+            s_b, c_b = timed(e, 3)
+        batch = {"chains": nbt, "L": Lb, "chi_max": chib, "ms_per_step": 1e3 * s_b / 3,
+                 "updates_per_s": c_b["layer_updates"] / s_b,
+                 "bond_kernel_tflops": c_b["layer_flops"] / s_b / 1e12,
+                 "alu_frac": c_b["layer_flops"] / s_b / 1e12 / alu_peak}
+    return {"workload": workload,
+            "time_to_solution": {"T": steps * rates["dt"], "steps": steps, "precision": "mixed",
+                                 "s": s_tts, "ms_per_step": 1e3 * s_tts / steps,
+                                 "updates_per_s": c_tts["layer_updates"] / s_tts,
+                                 "final_max_bond_dim": int(dims_end.max()),
+                                 "final_density_range": [float(n_end.min()), float(n_end.max())]},
+            "saturated_chi%d" % chi: sat, "mixed_vs_fp64": acc, "batch": batch,
+            "cpu_oracle": None if args.no_cpu else dm_cpu_oracle(args.cpu_seconds / 2, name, L,
+                                                                 chi, rates, init)}
 
 
 def run_reference(args):
@@ -434,76 +510,22 @@ def run_ours(args):
             e8.close()
             del m8, p8
 
-    # ---- vectorised density matrix leg (Sec. 3.1), one GPU -----------------------------
-    mpdo_leg = None
+    # ---- density-matrix legs: vectorised (Sec. 3.1) and purified (Sec. 3.2), one GPU ---
+    mpdo_leg = purified_leg = None
     if args.mpdo_steps > 0 and solo:
-        Lm, chim, dtm = 32, 64, 0.02
-        kwm = dict(method=lt.LT_MPDO, init="domain_wall", dt=dtm, gamma_loss=0.1,
-                   gamma_gain=0.05, fermionic_jumps=0, stream=stream.cuda_stream)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-
-        def timed(e, n):
-            torch.cuda.synchronize()
-            e.counters(clear=True)
-            ev[0].record(stream)
-            lt.lt_step(e.ctx, n)
-            ev[1].record(stream)
-            torch.cuda.synchronize()
-            return ev[0].elapsed_time(ev[1]) / 1e3, e.counters()
-
-        # time to solution: T = steps x dt from the domain wall, one chain, mixed
-        with lt.Ensemble(Lm, chim, 1, precision=lt.LT_MIXED, svd_cut=1e-6, **kwm) as e:
-            s_tts, c_tts = timed(e, args.mpdo_steps)
-            n_end = e.density()[0]
-            _, dims_end = e.stats()
-        # per-step cost of the saturated chain in both precisions
-        sat = {}
-        state = random_mpdo(Lm, chim, 99)
-        for name, prec, cut in (("mixed", lt.LT_MIXED, 1e-6), ("fp64", lt.LT_FP64, 1e-12)):
-            with lt.Ensemble(Lm, chim, 1, precision=prec, svd_cut=cut, **kwm) as e:
-                e.set_state(0, [state])
-                s_sat, c_sat = timed(e, args.mpdo_sat_steps)
-            tfl = c_sat["layer_flops"] / s_sat / 1e12
-            sat[name] = {"ms_per_step": 1e3 * s_sat / args.mpdo_sat_steps,
-                         "updates_per_s": c_sat["layer_updates"] / s_sat,
-                         "bond_kernel_tflops": tfl, "alu_frac": tfl / alu_peak}
-        # mixed against FP64 from the domain wall
-        acc = None
-        if args.mpdo_acc_steps > 0:
-            out = {}
-            for name, prec, cut in (("mixed", lt.LT_MIXED, 1e-6), ("fp64", lt.LT_FP64, 1e-12)):
-                with lt.Ensemble(Lm, chim, 1, precision=prec, svd_cut=cut, **kwm) as e:
-                    e.step(args.mpdo_acc_steps)
-                    out[name] = (e.density()[0], e.corr()[0])
-            acc = {"steps": args.mpdo_acc_steps,
-                   "max_abs_density": float(np.abs(out["mixed"][0] - out["fp64"][0]).max()),
-                   "max_abs_corr": float(np.abs(out["mixed"][1] - out["fp64"][1]).max())}
-        # a batch of independent chains (chi = 32: theta 128 x 128, register path)
-        batch = None
-        if args.mpdo_batch > 0:
-            nbt, Lb, chib = args.mpdo_batch, 24, 32
-            with lt.Ensemble(Lb, chib, nbt, precision=lt.LT_MIXED, svd_cut=1e-6, **kwm) as e:
-                e.set_state(0, [random_mpdo(Lb, chib, 7)] * nbt)
-                lt.lt_step(e.ctx, 1)
-                s_b, c_b = timed(e, 3)
-            batch = {"chains": nbt, "L": Lb, "chi_max": chib, "ms_per_step": 1e3 * s_b / 3,
-                     "updates_per_s": c_b["layer_updates"] / s_b,
-                     "bond_kernel_tflops": c_b["layer_flops"] / s_b / 1e12,
-                     "alu_frac": c_b["layer_flops"] / s_b / 1e12 / alu_peak}
-        mpdo_leg = {"workload": "MPDO (d^2 = 4): L=32 XX chain, spin loss 0.1 and gain 0.05 on "
-                                "every site, dt=0.02, 2nd-order Trotter, domain-wall start, "
-                                "chi_max=64 (the largest this build holds; the configuration "
-                                "names 128)",
-                    "time_to_solution": {"T": args.mpdo_steps * dtm, "steps": args.mpdo_steps,
-                                         "precision": "mixed", "s": s_tts,
-                                         "ms_per_step": 1e3 * s_tts / args.mpdo_steps,
-                                         "updates_per_s": c_tts["layer_updates"] / s_tts,
-                                         "final_max_bond_dim": int(dims_end.max()),
-                                         "final_density_range": [float(n_end.min()),
-                                                                 float(n_end.max())]},
-                    "saturated_chi64": sat, "mixed_vs_fp64": acc, "batch": batch,
-                    "cpu_oracle": None if args.no_cpu else mpdo_cpu_oracle(
-                        args.cpu_seconds / 2, Lm, chim, kwm)}
+        mpdo_leg = density_matrix_leg(
+            lt, stream, args, alu_peak, method=lt.LT_MPDO, L=32, chi=64, init="domain_wall",
+            rates=dict(dt=0.02, gamma_loss=0.1, gamma_gain=0.05), steps=args.mpdo_steps,
+            workload="MPDO (d^2 = 4): L=32 XX chain, spin loss 0.1 and gain 0.05 on every site, "
+                     "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=64 (the largest this "
+                     "build holds; the configuration names 128)")
+    if args.purified_steps > 0 and solo:
+        purified_leg = density_matrix_leg(
+            lt, stream, args, alu_peak, method=lt.LT_PURIFIED, L=64, chi=64, init="neel",
+            rates=dict(dt=0.01, gamma_loss=0.05, gamma_deph=0.1), steps=args.purified_steps,
+            workload="purified rho = X X^+ (physical d = 2, Kraus dimension 2): L=64 XX chain, "
+                     "dephasing 0.1 and spin loss 0.05 on every site, dt=0.01, 2nd-order Trotter "
+                     "then the R step, Neel start, chi_max=64 (the configuration names 96)")
 
     # ---- serving: Poisson arrivals of mixed requests through the request server --------
     serving = None
@@ -664,6 +686,7 @@ def run_ours(args):
             "mixed_vs_fp64": accuracy,
             "qsd": qsd,
             "mpdo": mpdo_leg,
+            "purified": purified_leg,
             "serving": serving,
             "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
         }
