@@ -240,6 +240,7 @@ def density_matrix_leg(lt, stream, args, alu_peak, method, L, chi, init, rates, 
     """Time to solution of one chain in mixed precision, the per-step cost of the
     saturated chain in both precisions, mixed against FP64 over the first steps,
     a batch of 148 chains at chi = 32 (theta 128 x 128), and the oracle."""
+    import torch
     name = "mpdo" if method == lt.LT_MPDO else "purified"
     kw = dict(method=method, init=init, fermionic_jumps=0, stream=stream.cuda_stream, **rates)
     if method == lt.LT_PURIFIED:
