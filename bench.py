@@ -329,9 +329,11 @@ def run_reference(args):
 
 
 # DRAM bytes (read + write) of one Trotter-layer launch of bond_update_kernel<float>
-# on the 4096-trajectory workload, from one ncu capture of the current kernel
-# (profiles/launches_w3s_4096traj.md); reported only for that workload.
-LAYER_LAUNCH_DRAM_BYTES = 12725311232 + 12486851584
+# on the 4096-trajectory workload from the last ncu capture
+# (profiles/launches_w3s_4096traj.md).  The kernel has changed since (templated on
+# the physical dimension, reflector phases from the scaled leading entry), so the
+# line reports traffic as null and this figure only as the last capture.
+LAYER_LAUNCH_DRAM_BYTES_LAST_CAPTURE = 12725311232 + 12486851584
 
 
 def algorithmic_tflops(flops, seconds):
@@ -673,10 +675,13 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "bond_update_kernel<float>",
                          "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak,
-                         "traffic": LAYER_LAUNCH_DRAM_BYTES if n_traj == 4096 and world == 1 else None,
-                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                         "Trotter-layer launch (ncu, this kernel, 4096 "
-                                         "trajectories): 192 KB per update",
+                         "traffic": None,
+                         "traffic_last_capture": LAYER_LAUNCH_DRAM_BYTES_LAST_CAPTURE
+                         if n_traj == 4096 and world == 1 else None,
+                         "traffic_note": "null: the kernel changed after the last capture; "
+                                         "that capture (dram__bytes_read.sum + "
+                                         "dram__bytes_write.sum of one Trotter-layer launch, "
+                                         "4096 trajectories) gave 25.2 GB, 192 KB per update",
                          "peak_source": "FP32 FMA lanes: 148 SM x 128 x 2 flop x sm_max_mhz "
                                         "(%s clock)" % src,
                          "mean_layer_ms": mean_layer_s * 1e3,
