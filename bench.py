@@ -537,16 +537,23 @@ def run_ours(args):
         n_req, rate = args.serve_requests, args.serve_rate
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
         reqs = []
+        methods = (lt.LT_TRAJ, lt.LT_QSD, lt.LT_MPDO, lt.LT_PURIFIED)
         for i in range(n_req):
-            qsd_req = bool(rng.integers(2))
+            method = methods[int(rng.integers(4))]
+            dm = method in (lt.LT_MPDO, lt.LT_PURIFIED)
             kw = dict(n_steps=int(rng.integers(10, 31)), L=int(rng.choice([16, 32, 64, 128])),
-                      chi_max=int(rng.choice([32, 64, 128])), n_traj=int(rng.choice([1, 8, 32, 128])),
-                      precision=lt.LT_MIXED, method=lt.LT_QSD if qsd_req else lt.LT_TRAJ,
-                      dt=0.02, seed=100 + i, svd_cut=1e-6, init="neel")
-            if qsd_req:
+                      chi_max=int(rng.choice([32, 64] if dm else [32, 64, 128])),
+                      n_traj=int(rng.choice([1, 2, 4] if dm else [1, 8, 32, 128])),
+                      precision=lt.LT_MIXED, method=method, dt=0.02, seed=100 + i, svd_cut=1e-6,
+                      init="neel")
+            if method == lt.LT_TRAJ:
+                kw.update(gamma_loss=0.1)
+            elif method == lt.LT_QSD:
                 kw.update(gamma_deph=0.1, gamma_loss=0.05, fermionic_jumps=0)
             else:
-                kw.update(gamma_loss=0.1)
+                kw.update(gamma_loss=0.1, gamma_gain=0.05, gamma_deph=0.02, fermionic_jumps=0)
+                if method == lt.LT_PURIFIED:
+                    kw["kraus_dim"] = 2
             reqs.append(kw)
         failed = {}
         with lt.Server(args.serve_budget_gb << 30, 64) as srv:
@@ -575,10 +582,11 @@ def run_ours(args):
                    "completed_per_s": len(lat) / wall,
                    "latency_s": {"p50": float(np.percentile(lat, 50)),
                                  "p99": float(np.percentile(lat, 99))} if lat else None,
-                   "mix": "trajectory or QSD (1:1), L in {16,32,64,128}, chi_max in "
-                          "{32,64,128}, 1..128 trajectories, 10..30 steps of dt=0.02, mixed "
-                          "precision, Neel start; Poisson arrivals; latency from submission to "
-                          "completion",
+                   "mix": "trajectory, QSD, MPDO or purified (1:1:1:1), L in {16,32,64,128}, "
+                          "chi_max in {32,64,128} (density matrices {32,64}), 1..128 "
+                          "trajectories (density matrices 1..4 chains), 10..30 steps of "
+                          "dt=0.02, mixed precision, Neel start; Poisson arrivals; latency from "
+                          "submission to completion",
                    "budget_gb": args.serve_budget_gb}
 
     # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------

@@ -18,6 +18,9 @@ REQUESTS = [
     # a vectorised density matrix: two chains, spin loss and gain on every site
     dict(n_steps=6, L=10, chi_max=16, n_traj=2, precision=1, method=2, dt=0.05,
          gamma_loss=0.1, gamma_gain=0.05, fermionic_jumps=0, seed=5, init="domain_wall"),
+    # a purified density matrix (Kraus dimension 2)
+    dict(n_steps=5, L=9, chi_max=16, n_traj=1, precision=0, method=3, kraus_dim=2, dt=0.05,
+         gamma_loss=0.1, gamma_deph=0.07, fermionic_jumps=0, seed=6),
 ]
 
 
@@ -60,7 +63,7 @@ def test_staggered_arrivals_of_different_chi():
     """Requests admitted while others run (a large-chi request first, smaller ones
     arriving during it) all finish with the results they give alone."""
     from paper_2609_18841_b300 import lindtebd as lt
-    order = [3, 0, 4, 2, 1]
+    order = [3, 0, 4, 5, 2, 1]
     alone = {i: _alone(lt, REQUESTS[i]) for i in order}
     with lt.Server(8 << 30, 16) as s:
         ids = {}
@@ -78,7 +81,8 @@ def test_staggered_arrivals_of_different_chi():
 def test_admission_cap_estimate_and_oversize():
     from paper_2609_18841_b300 import lindtebd as lt
     sizes = [lt.lt_context_bytes(r["L"], r["chi_max"], r["n_traj"], num_sms=148,
-                                 precision=r["precision"], method=r.get("method", 0))
+                                 precision=r["precision"], method=r.get("method", 0),
+                                 kraus_dim=r.get("kraus_dim", 0))
              for r in REQUESTS]
     alone = [_alone(lt, r) for r in REQUESTS]
     # one at a time (active cap 1) under a budget that fits the largest request
