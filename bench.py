@@ -491,7 +491,7 @@ def run_ours(args):
                "ms_per_step": 1e3 * sq / args.qsd_steps, "steps": args.qsd_steps,
                "log_weight_range": [float(lw.min()), float(lw.max())]}
         eq.close()
-        # the configuration's own chi_max = 128 (theta up to 256 x 256), fewer histories
+        # chi_max = 128 (theta up to 256 x 256, the generic paths), fewer histories
         if args.qsd_chi128_traj > 0:
             n8 = args.qsd_chi128_traj
             m8, p8 = state_pool(Lq, 128, 8, seed=4321)
@@ -520,15 +520,16 @@ def run_ours(args):
             lt, stream, args, alu_peak, method=lt.LT_MPDO, L=32, chi=64, init="domain_wall",
             rates=dict(dt=0.02, gamma_loss=0.1, gamma_gain=0.05), steps=args.mpdo_steps,
             workload="MPDO (d^2 = 4): L=32 XX chain, spin loss 0.1 and gain 0.05 on every site, "
-                     "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=64 (the largest this "
-                     "build holds; the configuration names 128)")
+                     "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=64 (theta up to "
+                     "256 x 256, the library's limit; chi_max = 128 would need 512 x 512)")
     if args.purified_steps > 0 and solo:
         purified_leg = density_matrix_leg(
             lt, stream, args, alu_peak, method=lt.LT_PURIFIED, L=64, chi=64, init="neel",
             rates=dict(dt=0.01, gamma_loss=0.05, gamma_deph=0.1), steps=args.purified_steps,
             workload="purified rho = X X^+ (physical d = 2, Kraus dimension 2): L=64 XX chain, "
                      "dephasing 0.1 and spin loss 0.05 on every site, dt=0.01, 2nd-order Trotter "
-                     "then the R step, Neel start, chi_max=64 (the configuration names 96)")
+                     "then the R step, Neel start, chi_max=64 (theta up to 256 x 256, the "
+                     "library's limit; chi_max = 96 would need 384 x 384)")
 
     # ---- serving: Poisson arrivals of mixed requests through the request server --------
     serving = None
