@@ -123,3 +123,34 @@ def test_chain_of_64_sites_sampled():
             _, Cp = e.corr(per_traj=True)
         close(per[0], res["density"], tol, "density")
         close(Cp[0], res["corr"], tol, "corr")
+
+
+def _edge_cases():
+    def ss(L, chi, order=2):
+        c = source_sink(L, chi, g=0.5, deph=0.1)
+        c.trotter_order = order
+        return c
+    spin = cfg_of(5, 8, loss=0.3, gain=0.12, deph=0.07, occ="domain_wall")
+    spin.trotter_order = 1
+    return [("one_bond_source_sink", ss(2, 4), 6), ("odd_first_order", ss(3, 8, order=1), 6),
+            ("chi_1", cfg_of(6, 1, loss=0.2, gain=0.1, deph=0.05), 5),
+            ("first_order_spin", spin, 7)]
+
+
+@pytest.mark.parametrize("name,cfg,steps", _edge_cases(), ids=[c[0] for c in _edge_cases()])
+def test_purified_edges(name, cfg, steps):
+    lt = _lt()
+    res = purified.run_purified(cfg, 2, steps, measure_corr=True)
+    with lt.Ensemble(cfg.L, cfg.chi_max, 1, method=lt.LT_PURIFIED, kraus_dim=2,
+                     precision=lt.LT_FP64, init="product",
+                     product_occ=cfg.occupation.astype(np.uint8), J=cfg.J, dt=cfg.dt,
+                     trotter_order=cfg.trotter_order, gamma_loss=cfg.gamma_loss,
+                     gamma_gain=cfg.gamma_gain, gamma_deph=cfg.gamma_deph,
+                     fermionic_jumps=int(cfg.fermionic), svd_cut=cfg.svd_cut) as e:
+        e.step(steps)
+        _, _, per = e.density(per_traj=True)
+        _, Cp = e.corr(per_traj=True)
+        _, dims = e.stats()
+    close(per[0], res["density"], FP64_TOL, "density")
+    close(Cp[0], res["corr"], FP64_TOL, "corr")
+    assert list(dims[0]) == list(res["bond_dims"])
