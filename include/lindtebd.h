@@ -184,6 +184,17 @@ lt_status lt_get_log_weights(lt_ctx ctx, double* out);
  * then lt_apply_kraus. */
 lt_status lt_step(lt_ctx ctx, int32_t n_steps);
 
+/* The same n_steps time steps as lt_step, replayed from a CUDA graph: the first
+ * call uploads the schedule's gates, captures one step's launches on the
+ * context's stream (their Philox step is read from a device counter that the
+ * captured step advances) and instantiates it; every call then replays it
+ * n_steps times.  Results are bit-identical to lt_step, and the two can be
+ * interleaved (the step counter is shared).  The graph saves the host launch
+ * cost of the roughly 2L + 7 kernels of a step (trajectory method), which
+ * matters for small ensembles.  LT_ERR_UNSUPPORTED if the stream cannot be
+ * captured (the legacy default stream). */
+lt_status lt_step_graph(lt_ctx ctx, int32_t n_steps);
+
 /* Ensemble density <n_i> = <psi|n_i|psi>/<psi|psi> (exact environments).
  * mean: [L] average over trajectories; sem: [L] CLT error sqrt(var/n_traj)
  * (Eq. ErrorCLT), or NULL; per_traj: [n_traj * L] row-major, or NULL.  For

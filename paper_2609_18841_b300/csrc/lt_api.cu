@@ -321,7 +321,7 @@ void free_all(lt_ctx_s* c) {
   void* ptrs[] = {c->B, c->lam, c->dims, c->trunc, c->evolve, c->channel, c->replay,
                   c->active_list, c->jumped_list, c->counts, c->density, c->logw, c->rates, c->gam,
                   c->err_dev, c->sweep_hist, c->counters, c->gates, c->bond_scratch, c->env_scratch,
-                  c->corr, c->red};
+                  c->corr, c->red, c->step_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -544,6 +544,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
 lt_status lt_destroy(lt_ctx c) {
   if (!c) return LT_ERR_ARG;
   cudaStreamSynchronize(c->stream);
+  if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
   free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -633,33 +634,100 @@ lt_status lt_get_log_weights(lt_ctx c, double* out) {
   return check_device_error(c);
 }
 
+// the launches of one time step (no host synchronisation once the gates are cached)
+static lt_status one_step(lt_ctx c, long long step) {
+  lt_status st;
+  if (c->method == LT_TRAJ) {
+    st = lt_apply_jumps(c, step, nullptr, nullptr);
+    if (st != LT_OK) return st;
+  }
+  if (c->order == 1) {
+    if ((st = lt_apply_layer(c, 0, c->dt)) != LT_OK) return st;
+    if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
+  } else {
+    if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
+    if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
+    if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
+  }
+  if (c->method == LT_QSD) {
+    st = lt_apply_noise(c, step);
+    if (st != LT_OK) return st;
+  }
+  if (c->method == LT_PURIFIED) {
+    st = lt_apply_kraus(c);
+    if (st != LT_OK) return st;
+  }
+  return LT_OK;
+}
+
 lt_status lt_step(lt_ctx c, int32_t n_steps) {
   lt_status st = guard(c);
   if (st != LT_OK) return st;
   if (n_steps < 0) return LT_ERR_ARG;
   for (int s = 0; s < n_steps; ++s) {
-    if (c->method == LT_TRAJ) {
-      st = lt_apply_jumps(c, c->step_counter, nullptr, nullptr);
-      if (st != LT_OK) return st;
-    }
-    if (c->order == 1) {
-      if ((st = lt_apply_layer(c, 0, c->dt)) != LT_OK) return st;
-      if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
-    } else {
-      if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
-      if ((st = lt_apply_layer(c, 1, c->dt)) != LT_OK) return st;
-      if ((st = lt_apply_layer(c, 0, 0.5 * c->dt)) != LT_OK) return st;
-    }
-    if (c->method == LT_QSD) {
-      st = lt_apply_noise(c, c->step_counter);
-      if (st != LT_OK) return st;
-    }
-    if (c->method == LT_PURIFIED) {
-      st = lt_apply_kraus(c);
-      if (st != LT_OK) return st;
-    }
+    st = one_step(c, c->step_counter);
+    if (st != LT_OK) return st;
     c->step_counter++;
   }
+  return LT_OK;
+}
+
+lt_status lt_step_graph(lt_ctx c, int32_t n_steps) {
+  lt_status st = guard(c);
+  if (st != LT_OK) return st;
+  if (n_steps < 0) return LT_ERR_ARG;
+  if (n_steps == 0) return LT_OK;
+  if (!c->step_graph) {
+    // the gates of the schedule are uploaded before the capture: an upload
+    // synchronises the stream, which a capture does not allow
+    const double2* g = nullptr;
+    if (c->order == 1) {
+      if ((st = gate_ptr(c, c->dt, &g)) != LT_OK) return st;
+    } else {
+      if ((st = gate_ptr(c, 0.5 * c->dt, &g)) != LT_OK) return st;
+      if ((st = gate_ptr(c, c->dt, &g)) != LT_OK) return st;
+    }
+    if (!c->step_dev) {
+      st = dalloc(c, &c->step_dev, 1);
+      if (st != LT_OK) return st;
+    }
+    cudaGraph_t graph = nullptr;
+    const long long before = c->launches;
+    c->use_step_dev = true;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      c->use_step_dev = false;
+      cudaGetLastError();
+      c->last_error = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+      return LT_ERR_UNSUPPORTED;  // e.g. the legacy default stream
+    }
+    st = one_step(c, 0);
+    cudaError_t e2 = st == LT_OK ? launch_step_advance(c) : cudaSuccess;
+    e = cudaStreamEndCapture(c->stream, &graph);
+    c->use_step_dev = false;
+    if (st != LT_OK || e2 != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      c->launches = before;
+      if (st != LT_OK) return st;
+      return fail(c, LT_ERR_CUDA, "step capture", cudaGetErrorString(e2 != cudaSuccess ? e2 : e));
+    }
+    e = cudaGraphInstantiate(&c->step_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->step_graph = nullptr;
+      c->launches = before;
+      return fail(c, LT_ERR_CUDA, "cudaGraphInstantiate", cudaGetErrorString(e));
+    }
+    c->graph_launches = c->launches - before;
+    c->launches = before;
+  }
+  // the device counter starts at this context's step; each replay advances it
+  c->step_host = c->step_counter;
+  LT_CK(cudaMemcpyAsync(c->step_dev, &c->step_host, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+  for (int s = 0; s < n_steps; ++s) LT_CK(cudaGraphLaunch(c->step_graph, c->stream));
+  c->step_counter += n_steps;
+  c->launches += (long long)n_steps * c->graph_launches;
   return LT_OK;
 }
 

@@ -177,6 +177,7 @@ struct EnvArgs {
   uint64_t seed;
   long long traj_offset;
   long long step;
+  const long long* step_dev;  // the step from device memory (captured steps), or nullptr
   int* err;
   double2* corr;        // [n_traj][L][L] for the correlation kernel
 };
@@ -246,6 +247,12 @@ struct lt_ctx_s {
 
   long long step_counter;
   long long launches;
+  // a captured time step (lt_step_graph): its launches read the step from step_dev
+  long long* step_dev;
+  bool use_step_dev;
+  cudaGraphExec_t step_graph;
+  long long graph_launches;   // kernels per captured step
+  long long step_host;        // source of the counter upload (outlives the async copy)
   size_t dev_bytes;   // device memory this context allocated
   bool poisoned;
   std::string last_error;
@@ -262,6 +269,7 @@ cudaError_t launch_corr(lt_ctx_s* c);
 cudaError_t launch_mpdo_trace(lt_ctx_s* c, bool corr);
 size_t mpdo_scratch_bytes(int L, int chi);
 cudaError_t launch_kraus(lt_ctx_s* c);
+cudaError_t launch_step_advance(lt_ctx_s* c);
 cudaError_t launch_purified_env(lt_ctx_s* c, bool corr);
 size_t purified_scratch_bytes(int L, int chi);
 cudaError_t launch_reduce_density(lt_ctx_s* c, double* out_mean, double* out_sem);

@@ -1609,7 +1609,8 @@ __device__ void decide_channel(const EnvArgs& a, int traj) {
     double total = 0.0;
     for (int j = 0; j < 3 * L; ++j) total += rt[j] * a.dt;
     if (total >= 0.5) atomicOr(a.err, LT_EBIT_PROB);
-    const double r = philox_uniform(a.seed, (uint32_t)(a.traj_offset + traj), (uint64_t)a.step, 0u);
+    const long long step = a.step_dev ? *a.step_dev : a.step;
+    const double r = philox_uniform(a.seed, (uint32_t)(a.traj_offset + traj), (uint64_t)step, 0u);
     if (r < total) {
       double cs = 0.0;
       for (int j = 0; j < 3 * L; ++j) {
@@ -2008,10 +2009,11 @@ __global__ void reduce_mean_c_kernel(const double2* x, int n, int M, double* out
 template <typename R>
 __global__ void __launch_bounds__(128) qsd_noise_kernel(typename CT<R>::T* B, const int* dims, int L,
                                                         int slot, int n_traj, long long traj_offset,
-                                                        long long step, uint64_t seed,
-                                                        const double* gam, double dt) {
+                                                        long long step_arg, const long long* step_dev,
+                                                        uint64_t seed, const double* gam, double dt) {
   typedef typename CT<R>::T Tc;
   __shared__ double sM[4];
+  const long long step = step_dev ? *step_dev : step_arg;
   const long long ntask = (long long)n_traj * L;
   for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
     const int traj = (int)(task / L), i = (int)(task - (long long)traj * L);
@@ -2728,6 +2730,7 @@ static EnvArgs env_args(lt_ctx_s* c) {
   a.seed = c->seed;
   a.traj_offset = c->traj_offset;
   a.step = 0;
+  a.step_dev = c->use_step_dev ? c->step_dev : nullptr;
   a.err = c->err_dev;
   a.corr = c->corr;
   return a;
@@ -2813,6 +2816,17 @@ cudaError_t launch_purified_env(lt_ctx_s* c, bool corr) {
   return cudaGetLastError();
 }
 
+// the step counter of a captured time step advances on the device
+__global__ void step_advance_kernel(long long* step_dev) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step_dev += 1;
+}
+
+cudaError_t launch_step_advance(lt_ctx_s* c) {
+  step_advance_kernel<<<1, 32, 0, c->stream>>>(c->step_dev);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_jump_apply(lt_ctx_s* c) {
   const int grid = c->n_traj < 4 * c->num_sms ? c->n_traj : 4 * c->num_sms;
   if (c->prec == LT_MIXED)
@@ -2855,11 +2869,13 @@ cudaError_t launch_qsd_noise(lt_ctx_s* c, long long step) {
   if (c->prec == LT_MIXED)
     qsd_noise_kernel<float><<<grid, 128, 0, c->stream>>>(reinterpret_cast<float2*>(c->B), c->dims, c->L,
                                                           c->slot, c->n_traj, c->traj_offset, step,
+                                                          c->use_step_dev ? c->step_dev : nullptr,
                                                           c->seed, c->gam, c->dt);
   else
     qsd_noise_kernel<double><<<grid, 128, 0, c->stream>>>(reinterpret_cast<double2*>(c->B), c->dims,
                                                            c->L, c->slot, c->n_traj, c->traj_offset,
-                                                           step, c->seed, c->gam, c->dt);
+                                                           step, c->use_step_dev ? c->step_dev : nullptr,
+                                                           c->seed, c->gam, c->dt);
   c->launches++;
   return cudaGetLastError();
 }

@@ -38,7 +38,7 @@ class lt_config(ctypes.Structure):
 
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
            "lt_apply_kraus", "lt_get_log_weights",
-           "lt_step", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
+           "lt_step", "lt_step_graph", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
            "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
@@ -59,6 +59,7 @@ def load_library(path=LIB_PATH):
         "lt_apply_kraus": ([P], I32),
         "lt_get_log_weights": ([P, P], I32),
         "lt_step": ([P, I32], I32),
+        "lt_step_graph": ([P, I32], I32),
         "lt_measure_density": ([P, P, P, P], I32),
         "lt_measure_corr": ([P, P, P, P, P], I32),
         "lt_get_stats": ([P, P, P], I32),
@@ -180,6 +181,10 @@ def lt_get_log_weights(ctx, n_traj):
 
 def lt_step(ctx, n_steps):
     _check(_lib.lt_step(ctx, n_steps), "lt_step", ctx)
+
+
+def lt_step_graph(ctx, n_steps):
+    _check(_lib.lt_step_graph(ctx, n_steps), "lt_step_graph", ctx)
 
 
 def lt_measure_density(ctx, L, n_traj, per_traj=False, out=None):
@@ -319,6 +324,9 @@ class Ensemble:
 
     def step(self, n=1):
         lt_step(self.ctx, n)
+
+    def step_graph(self, n=1):
+        lt_step_graph(self.ctx, n)
 
     def apply_jumps(self, step, replay=None, want_channels=True):
         return lt_apply_jumps(self.ctx, step, replay, self.n_traj, want_channels)
