@@ -65,6 +65,8 @@ def test_status_strings_and_null_context():
         assert lt._lib.lt_status_str(s)
     assert lt._lib.lt_destroy(None) == lt.LT_ERR_ARG
     assert lt._lib.lt_step(None, 1) == lt.LT_ERR_ARG
+    assert lt._lib.lt_step_graph(None, 1) == lt.LT_ERR_ARG
+    assert lt._lib.lt_apply_kraus(None) == lt.LT_ERR_ARG
     assert lt._lib.lt_launch_count(None) == 0
     out = ctypes.c_void_p(1)
     assert lt._lib.lt_create(None, None, ctypes.byref(out)) == lt.LT_ERR_ARG
