@@ -139,6 +139,16 @@ lt_status lt_apply_layer(lt_ctx ctx, int32_t parity, double tau);
 lt_status lt_apply_jumps(lt_ctx ctx, int64_t step, const int32_t* replay,
                          int32_t* out_channel);
 
+/* Host only (no device work): the two-site gates a context of cfg would build for
+ * time step tau, as lt_apply_layer applies them.  out receives (L-1) matrices of
+ * D^2 x D^2 complex entries, interleaved (re, im) doubles, bond b at
+ * b * 2 D^4, row-major over (s_b, s_{b+1}) x (t_b, t_{b+1}): D = 2 for LT_TRAJ and
+ * LT_QSD (exp(-i h_b^eff tau)), D = 4 for LT_MPDO (exp(tau Lv_b), Eq. Liouvillian
+ * on m = 2n + n') and LT_PURIFIED (exp(-i h_b^eff tau) (x) 1 over the Kraus
+ * indices, s = 2n + k).  capacity: doubles available at out (at least
+ * 2 D^4 (L-1)), else LT_ERR_ARG. */
+lt_status lt_gates(const lt_config* cfg, double tau, double* out, int64_t capacity);
+
 /* Quantum state diffusion noise of time step `step` (Sec. 5.2, LT_QSD
  * contexts; LT_ERR_UNSUPPORTED otherwise).  The scheme iterates
  * |psi> <- prod_k (1 + eta_k sqrt(gamma_k dt) L_k) exp(-i H_eff dt) |psi> on

@@ -672,6 +672,37 @@ lt_status lt_step(lt_ctx c, int32_t n_steps) {
   return LT_OK;
 }
 
+lt_status lt_gates(const lt_config* cfg, double tau, double* out, int64_t capacity) {
+  if (!cfg || !out || cfg->L < 2 || cfg->L > 1024 || !std::isfinite(tau) || !std::isfinite(cfg->J))
+    return LT_ERR_ARG;
+  if (cfg->method < LT_TRAJ || cfg->method > LT_PURIFIED) return LT_ERR_UNSUPPORTED;
+  lt_ctx_s c{};
+  c.L = cfg->L;
+  c.J = cfg->J;
+  c.method = cfg->method;
+  c.d = cfg->method == LT_MPDO || cfg->method == LT_PURIFIED ? 4 : 2;
+  c.gl.assign(c.L, 0.0);
+  c.gg.assign(c.L, 0.0);
+  c.gd.assign(c.L, 0.0);
+  for (int i = 0; i < c.L; ++i) {
+    if (cfg->gamma_loss) c.gl[i] = cfg->gamma_loss[i];
+    if (cfg->gamma_gain) c.gg[i] = cfg->gamma_gain[i];
+    if (cfg->gamma_deph) c.gd[i] = cfg->gamma_deph[i];
+    if (!(c.gl[i] >= 0.0) || !(c.gg[i] >= 0.0) || !(c.gd[i] >= 0.0)) return LT_ERR_ARG;
+  }
+  const int64_t per = (int64_t)c.d * c.d * c.d * c.d;
+  if (capacity < 2 * per * (c.L - 1)) return LT_ERR_ARG;
+  std::vector<double2> g;
+  if (c.method == LT_MPDO) build_liouvillian_gates(&c, tau, g);
+  else if (c.method == LT_PURIFIED) build_purified_gates(&c, tau, g);
+  else build_gates(&c, tau, g);
+  for (size_t i = 0; i < g.size(); ++i) {
+    out[2 * i] = g[i].x;
+    out[2 * i + 1] = g[i].y;
+  }
+  return LT_OK;
+}
+
 lt_status lt_step_graph(lt_ctx c, int32_t n_steps) {
   lt_status st = guard(c);
   if (st != LT_OK) return st;

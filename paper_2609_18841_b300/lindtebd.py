@@ -38,7 +38,7 @@ class lt_config(ctypes.Structure):
 
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
            "lt_apply_kraus", "lt_get_log_weights",
-           "lt_step", "lt_step_graph", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
+           "lt_step", "lt_step_graph", "lt_gates", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
            "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
@@ -60,6 +60,7 @@ def load_library(path=LIB_PATH):
         "lt_get_log_weights": ([P, P], I32),
         "lt_step": ([P, I32], I32),
         "lt_step_graph": ([P, I32], I32),
+        "lt_gates": ([ctypes.POINTER(lt_config), D, P, I64], I32),
         "lt_measure_density": ([P, P, P, P], I32),
         "lt_measure_corr": ([P, P, P, P, P], I32),
         "lt_get_stats": ([P, P, P], I32),
@@ -181,6 +182,16 @@ def lt_get_log_weights(ctx, n_traj):
 
 def lt_step(ctx, n_steps):
     _check(_lib.lt_step(ctx, n_steps), "lt_step", ctx)
+
+
+def lt_gates(L, tau, **kw):
+    """The gates a context of these settings builds for time step tau (host only):
+    (L-1, D^2, D^2) complex, D = 2 or 4 by method."""
+    cfg, keep = make_config(L, 1, 1, **kw)
+    D = 4 if cfg.method in (LT_MPDO, LT_PURIFIED) else 2
+    out = np.empty(2 * D ** 4 * (L - 1))
+    _check(_lib.lt_gates(ctypes.byref(cfg), tau, _ptr(out), out.size), "lt_gates")
+    return out.view(np.complex128).reshape(L - 1, D * D, D * D)
 
 
 def lt_step_graph(ctx, n_steps):
