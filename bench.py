@@ -187,6 +187,32 @@ def cpu_baseline(seconds, L=64, chi=64, tag="cpu_baseline"):
                       "(%d two-site updates, %.1f s)" % (n_traj, updates, dt)}
 
 
+def qsd_cpu_oracle(seconds, L, chi, dt, gamma_loss, gamma_deph):
+    """The FP64 QSD oracle as it stands: whole time steps of single histories of
+    the QSD workload (synthetic chi-saturated start states), until about `seconds`
+    of CPU work.  A step is the Trotter layers with the norm kept, the noise on
+    every site and the whole-chain re-canonicalisation."""
+    from oracle import tebd
+    cfg = tebd.TrajectoryConfig(L, J=1.0, dt=dt, chi_max=chi, svd_cut=1e-12,
+                                gamma_loss=gamma_loss, gamma_deph=gamma_deph, fermionic=False,
+                                occupation=workloads.occupation(L, "neel"), seed=7)
+    gates = tebd.StepGates(cfg)
+    per_step = sum(len(range(p, L - 1, 2)) for p, _ in cfg.layers()) + 2 * (L - 1)
+    updates, steps = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        B, lam, _ = workloads.synthetic_mps(L, chi, seed=4321 + steps % POOL)
+        tr = tebd.Trajectory.from_tensors(cfg, B, lam)
+        tebd.step_qsd(tr, gates, steps, 0)
+        updates += per_step
+        steps += 1
+    dt_ = time.perf_counter() - t0
+    return {"value": updates / dt_, "unit": UNIT, "kind": "oracle",
+            "sample": "%d histories x 1 QSD step of the L=%d, chi=%d workload from synthetic "
+                      "states (%d two-site updates incl. the re-canonicalisation, %.1f s)"
+                      % (steps, L, chi, updates, dt_)}
+
+
 def random_mpdo(L, chi, seed):
     """A synthetic vectorised density matrix with every bond at its full
     dimension min(chi, 4^min(b+1, L-b-1)): complex Gaussian site tensors of shape
@@ -487,10 +513,14 @@ def run_ours(args):
                            "states, mixed precision" % nq,
                "updates_per_s": cq["updates"] / sq,
                "layer_updates_per_s": cq["layer_updates"] / sq,
+               "bond_kernel_tflops": (cq["layer_flops"] + cq["sweep_flops"]) / sq / 1e12,
+               "alu_frac": (cq["layer_flops"] + cq["sweep_flops"]) / sq / 1e12 / alu_peak,
                "trajectory_steps_per_s": nq * args.qsd_steps / sq,
                "ms_per_step": 1e3 * sq / args.qsd_steps, "steps": args.qsd_steps,
                "log_weight_range": [float(lw.min()), float(lw.max())]}
         eq.close()
+        if not args.no_cpu:
+            qsd["cpu_oracle"] = qsd_cpu_oracle(args.cpu_seconds / 2, Lq, chi, dtq, 0.05, 0.1)
         # chi_max = 128 (theta up to 256 x 256, the generic paths), fewer histories
         if args.qsd_chi128_traj > 0:
             n8 = args.qsd_chi128_traj
