@@ -175,8 +175,9 @@ lt_status lt_apply_noise(lt_ctx ctx, int64_t step);
  * which turns sum_k A A^+ into the tensor R of Eq. MatrixR (rho -> rho + dt
  * sum_c gamma_c L_c rho L_c^+ on that site), and replaced by A~ V with V the two
  * leading eigenvectors of the Lambda_{i-1}-weighted Gram matrix A~^+ W^2 A~ (at
- * most 8 x 8, W the left Schmidt values: the site's environment in this gauge),
- * which are the leading eigenvectors of R scaled by sqrt(lambda).  In an
+ * most 8 x 8, W the left Schmidt values: the site's environment in this gauge);
+ * W A~ V are then the leading eigenvectors of W R W scaled by sqrt(lambda), the
+ * paper's R taken in that environment.  In an
  * LT_PURIFIED context lt_apply_layer applies exp(-i h_b^eff tau) (x) 1 over the
  * Kraus indices and keeps the norm change (B_b <- theta~ V_k), and lt_step runs
  * the layers, then this call. */
