@@ -329,7 +329,9 @@ lt_status lt_server_usage(lt_server server, uint64_t* used_bytes, uint64_t* budg
  * device, in the library's layout: B [n_traj][L][2 chi_max^2] complex
  * (float2 for LT_MIXED, double2 for LT_FP64, site i holding B_i[a][s][c]
  * row-major over its actual shape), dims [n_traj][L-1] int32 with
- * 1 <= dims <= chi_max, density [n_traj][L] double (written).  All three are
+ * 1 <= dims <= chi_max, density [n_traj][L] double (written; a trajectory
+ * with a dimension outside [1, chi_max] is skipped and its row set to NaN, the
+ * kernel checking the dimensions before it reads a site).  All three are
  * DEVICE pointers owned by the caller.  Work is queued on `stream` (a
  * cudaStream_t, NULL = the legacy default stream); the call does not
  * synchronise it and calls no cudaMalloc, cudaFree or allocating routine.
@@ -339,9 +341,11 @@ lt_status lt_server_usage(lt_server server, uint64_t* used_bytes, uint64_t* budg
  * needs (L + 8) * chi_max^2 complex elements of it, so the call returns
  * LT_ERR_ARG when (L + 8) chi_max^2 * 8 bytes (LT_MIXED) or * 16 bytes (LT_FP64)
  * exceeds 32 MiB (e.g. LT_FP64 with L > 504 at chi_max = 64), and LT_ERR_ARG for
- * any other invalid size or NULL pointer.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  Every call shares the one
+ * any other invalid size or NULL pointer.  Every call looks up the array's
+ * address on the current device (cudaGetSymbolAddress, which allocates
+ * nothing), so no address outlives a device reset; the first call on a device
+ * may load the library's device code, so make it before any stream capture.
+ * Every call shares the one
  * array and the kernel writes each scratch element before reading it, so
  * nothing needs clearing between calls; calls that overlap on the GPU (on
  * different streams, or from several threads) race on it and must be
@@ -349,6 +353,17 @@ lt_status lt_server_usage(lt_server server, uint64_t* used_bytes, uint64_t* budg
 lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, int32_t chi_max,
                                      int32_t n_traj, const void* B, const int32_t* dims,
                                      double* density, void* stream);
+
+/* Roofline denominators of the SIMT pipes on the current device (the paper has no
+ * counterpart; the measurement reports each kernel's arithmetic rate against them).
+ * A microbenchmark of independent fused multiply-add chains held in registers,
+ * four CTAs of 256 threads per SM, each kernel launched twice on an internal
+ * stream and the second launch timed with CUDA events (about 0.1 s in all).
+ * out[0]: single-precision TFLOP/s of packed FMA pairs (__ffma2_rn, 4 flops per
+ * instruction), out[1]: double-precision TFLOP/s of scalar FMAs, out[2]: the SM
+ * clock the device reports (MHz), out[3]: the number of SMs.  out: [4] host doubles.
+ * Synchronises the device's work on that stream only; allocates 2 KiB. */
+lt_status lt_pipe_peaks(double* out);
 
 /* Number of kernels this context has launched so far. */
 int64_t lt_launch_count(lt_ctx ctx);

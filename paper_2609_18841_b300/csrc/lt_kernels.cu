@@ -18,7 +18,6 @@
 #include <cfloat>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "lt_internal.cuh"
 
@@ -1190,6 +1189,80 @@ __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, i
 }
 
 
+
+// ---- re-orthonormalisation of V_k^+ (single precision) -----------------------------------
+// The one-sided Jacobi stops once every row pair is orthogonal to eps sqrt(r) |x| |y|,
+// so the rows v_j^+ it yields are orthonormal only to about that threshold (1e-6 at
+// r = 128), well above the rounding of the stored tensors; the split B_b = theta~ V_k,
+// B_{b+1} = V_k^+ then carries that defect into the state.  One step of the polar
+// (Lowdin) iteration removes it without changing the span of the kept rows: each row is
+// scaled to unit length by its norm accumulated in double, E = V^+ V - I is formed (zero
+// diagonal; the off-diagonal entries are of the order of the threshold, so their
+// single-precision rounding lies orders of magnitude below it) and V^+ <- (I - E/2) V^+,
+// which is orthonormal to O(|E|^2) plus the final rounding.  E is written to the
+// scratch array Es (k x k complex); the product runs in column chunks held in registers.
+template <int NT>
+__device__ void reorthonormalise_rows(float2* Y, int ld, int k, int n, float2* Es) {
+  constexpr int NW = NT / 32, PER = 16;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < k; j += NW) {
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) {
+      const float2 v = Y[j * ld + c];
+      acc = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, acc));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    const float sc = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.f;
+    for (int c = lane; c < n; c += 32) {
+      float2 v = Y[j * ld + c];
+      v.x *= sc;
+      v.y *= sc;
+      Y[j * ld + c] = v;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < k * k; idx += NT) {
+    const int i = idx / k, j = idx - i * k;
+    float2 acc = make_float2(0.f, 0.f);
+    if (i != j) {
+      const float2* yi = Y + i * ld;
+      const float2* yj = Y + j * ld;
+      for (int c = 0; c < n; ++c) cfmac(acc, yi[c], yj[c]);  // sum_c y_i conj(y_j)
+    }
+    Es[idx] = acc;
+  }
+  __syncthreads();
+  const int cw = (NT * PER) / k < n ? ((NT * PER) / k > 0 ? (NT * PER) / k : 1) : n;
+  for (int c0 = 0; c0 < n; c0 += cw) {
+    const int w = n - c0 < cw ? n - c0 : cw;
+    float2 acc[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      acc[p] = make_float2(0.f, 0.f);
+      const int idx = tid + NT * p;
+      if (idx < k * w) {
+        const int i = idx / w, c = c0 + idx - i * w;
+        const float2* e = Es + i * k;
+        for (int j = 0; j < k; ++j) cfma(acc[p], e[j], Y[j * ld + c]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int idx = tid + NT * p;
+      if (idx < k * w) {
+        const int i = idx / w, c = c0 + idx - i * w;
+        float2 v = Y[i * ld + c];
+        v.x = fmaf(-0.5f, acc[p].x, v.x);
+        v.y = fmaf(-0.5f, acc[p].y, v.y);
+        Y[i * ld + c] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---- the two-site update and the one-site canonical-form steps -----------------------------
 // mode 0: two-site update with the layer's gate (Eq. Theta): theta = Lambda_{b-1}
 //         G (B_b B_{b+1}), SVD, keep k, Lambda_b = S_k/|S_k|, B_{b+1} = V_k^+,
@@ -1454,6 +1527,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
     }
     __syncthreads();
+    // single precision: V_k^+ orthonormal to working precision (E in the free planes)
+    if constexpr (sizeof(R) == 4)
+      reorthonormalise_rows<BondShape<R>::NT>(reinterpret_cast<float2*>(Y), ld, k, nJ,
+                                              reinterpret_cast<float2*>(Xr));
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
       // B_b <- theta~ V_k (/ |S_k| in mode 0), B_{b+1} <- V_k^+
@@ -1759,6 +1836,26 @@ __global__ void __launch_bounds__(LT_BLOCK) env_tiled_kernel(EnvArgs a) {
   for (int traj = blockIdx.x; traj < a.n_traj; traj += gridDim.x) {
     const Tc* B = reinterpret_cast<const Tc*>(a.B) + (long long)traj * L * a.slot;
     const int* dm = a.dims + (long long)traj * (L - 1);
+    // bond dimensions outside [1, chi] would take the contractions past the site
+    // slots and the scratch: such a trajectory's densities become NaN, it draws
+    // no jump, and it is skipped (its dimensions come from the caller in
+    // lt_measure_density_noalloc)
+    int bad = 0;
+    for (int b = threadIdx.x; b < L - 1; b += blockDim.x) bad |= (dm[b] < 1 || dm[b] > chi);
+    if (__syncthreads_or(bad)) {
+      const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+      for (int k = threadIdx.x; k < L; k += blockDim.x) a.density[(long long)traj * L + k] = qnan;
+      if (kRates) {
+        for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) a.rates[(long long)traj * 3 * L + k] = 0.0;
+        if (threadIdx.x == 0) {
+          a.channel[traj] = -1;
+          a.evolve[traj] = 1;
+          if (a.err) atomicOr(a.err, LT_EBIT_BADARG);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     const double nrm2 = right_envs_tiled<R>(B, dm, L, chi, a.slot, Rl, T, sA, sB);
     if (threadIdx.x == 0) Le[0] = cmk<Tc>(1.0, 0.0);
     __syncthreads();
@@ -2956,13 +3053,8 @@ cudaError_t configure_bond(lt_ctx_s* c) {
 // call itself allocates nothing.  Every GPU that loads the library holds it until
 // the process exits.
 #define LT_NOALLOC_SCRATCH_BYTES (32ull << 20)
-#define LT_NOALLOC_MAX_DEVICES 64
 static __device__ __align__(256) unsigned char lt_noalloc_scratch[LT_NOALLOC_SCRATCH_BYTES];
 
-namespace {
-std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[LT_NOALLOC_MAX_DEVICES];
-}  // namespace
 
 extern "C" lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, int32_t chi_max,
                                                 int32_t n_traj, const void* B,
@@ -2977,19 +3069,12 @@ extern "C" lt_status lt_measure_density_noalloc(int32_t precision, int32_t L, in
   if (per_cta > LT_NOALLOC_SCRATCH_BYTES) return LT_ERR_ARG;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LT_ERR_CUDA;
-  if (dev < 0 || dev >= LT_NOALLOC_MAX_DEVICES) return LT_ERR_UNSUPPORTED;
+  // the host-side name of the array is only a stand-in: the kernel needs the
+  // device address on the current device, looked up on every call (no
+  // allocation), so nothing cached outlives a device reset
   void* scratch = nullptr;
-  {
-    // once per device, with that device current: the host-side name of the
-    // array is only a stand-in, the kernel needs its device address
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, lt_noalloc_scratch) != cudaSuccess || !p) return LT_ERR_CUDA;
-      g_noalloc_addr[dev] = p;
-    }
-    scratch = g_noalloc_addr[dev];
-  }
+  if (cudaGetSymbolAddress(&scratch, lt_noalloc_scratch) != cudaSuccess || !scratch)
+    return LT_ERR_CUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return LT_ERR_CUDA;
   long long grid = (long long)(LT_NOALLOC_SCRATCH_BYTES / per_cta);

@@ -59,3 +59,35 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert lt.lt_measure_density_noalloc(lt.LT_FP64, 8, 129, 1, p, p, p, None) == lt.LT_ERR_ARG
     assert lt.lt_measure_density_noalloc(lt.LT_MIXED, 8, 8, 1, p, None, p, None) == lt.LT_ERR_ARG
     assert lt.lt_measure_density_noalloc(lt.LT_FP64, 8, 8, 0, p, p, p, None) == lt.LT_ERR_ARG
+
+
+def test_noalloc_skips_trajectories_with_dimensions_out_of_range():
+    # the kernel checks every bond dimension of a trajectory against [1, chi_max]
+    # before it reads a site: a trajectory outside it gets NaN densities, the
+    # others are measured as usual
+    import torch
+    from paper_2609_18841_b300 import lindtebd as lt
+
+    L, chi, n = 10, 8, 4
+    states = [workloads.synthetic_mps(L, chi, seed=700 + t, ragged=True) for t in range(n)]
+    with lt.Ensemble(L, chi, n, precision=lt.LT_MIXED, init="neel", dt=0.05, gamma_loss=0.3,
+                     seed=3) as ens:
+        ens.set_state(0, states)
+        _, _, want = ens.density(per_traj=True)
+        dims, lam, B = ens.get_state(0, n)
+    dims = dims.copy()
+    dims[1, 3] = chi + 5
+    dims[3, 0] = 0
+    dev = torch.device("cuda", 0)
+    d_B = torch.from_numpy(B).to(device=dev, dtype=torch.complex64).contiguous()
+    d_dims = torch.from_numpy(dims).to(device=dev).contiguous()
+    d_out = torch.zeros((n, L), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = lt.lt_measure_density_noalloc(lt.LT_MIXED, L, chi, n, d_B.data_ptr(), d_dims.data_ptr(),
+                                       d_out.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    assert st == lt.LT_OK
+    got = d_out.cpu().numpy()
+    assert np.all(np.isnan(got[1])) and np.all(np.isnan(got[3]))
+    ok = [0, 2]
+    assert np.abs(got[ok] - want[ok]).max() <= TOL * max(1.0, float(np.abs(want).max()))
