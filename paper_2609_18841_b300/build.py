@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblindtebd.so")
-SOURCES = ["lt_api.cu", "lt_kernels.cu", "lt_server.cu"]
+SOURCES = ["lt_api.cu", "lt_kernels.cu", "lt_server.cu", "lt_peaks.cu"]
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-shared"]
 

@@ -39,7 +39,7 @@ class lt_config(ctypes.Structure):
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
            "lt_apply_kraus", "lt_get_log_weights",
            "lt_step", "lt_step_graph", "lt_gates", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
-           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step",
+           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step", "lt_pipe_peaks",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
            "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
            "lt_server_result", "lt_server_error", "lt_server_usage"]
@@ -72,6 +72,7 @@ def load_library(path=LIB_PATH):
         "lt_get_counters": ([P, P, I32], I32),
         "lt_measure_density_noalloc": ([I32, I32, I32, I32, P, P, P, P], I32),
         "lt_launch_count": ([P], I64),
+        "lt_pipe_peaks": ([P], I32),
         "lt_stream": ([P], P),
         "lt_get_step": ([P], I64),
         "lt_status_str": ([I32], ctypes.c_char_p),
@@ -269,6 +270,15 @@ def lt_measure_density_noalloc(precision, L, chi_max, n_traj, B_ptr, dims_ptr, d
     """Device pointers in, densities written to density_ptr; returns the status."""
     return int(_lib.lt_measure_density_noalloc(precision, L, chi_max, n_traj, B_ptr, dims_ptr,
                                                density_ptr, stream))
+
+
+def lt_pipe_peaks():
+    """Measured SIMT peaks of the current device: dict(fp32_tflops, fp64_tflops,
+    sm_clock_mhz, sms)."""
+    out = np.zeros(4)
+    _check(_lib.lt_pipe_peaks(_ptr(out)), "lt_pipe_peaks")
+    return dict(fp32_tflops=float(out[0]), fp64_tflops=float(out[1]),
+                sm_clock_mhz=float(out[2]), sms=int(out[3]))
 
 
 def lt_launch_count(ctx):
