@@ -19,6 +19,10 @@ Modules
   purified the locally purified density matrix rho = X X^+ (Sec. 3.2, Eqs.
            Purified, ThetaPurified, MatrixR, NewPurified): effective-Hamiltonian
            layers on X with a Kraus index per site, then the R step per site.
+  slater   the exact untruncated history of the free-fermion chain for a given
+           jump record: every gate and jump maps a Slater determinant to a
+           Slater determinant, so a history is N orbitals (Sec. 2.1, Sec. 4.1);
+           it sizes the truncation error of the MPS histories at any L.
   dense    brute-force references: the dense Trotterised state vector, dense
            Lindblad integration of rho, and the correlation-matrix equation of
            motion (Sec. 2.1 Eqs. eqCorr, SoleqCorr; Eq. Lindblad).
