@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--acc-steps", type=int, default=2)
+    ap.add_argument("--full-traj", type=int, default=512)
+    ap.add_argument("--full-exact", type=int, default=128)
+    ap.add_argument("--graph-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -152,39 +155,71 @@ def peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def cpu_baseline(seconds, L=64, chi=64, tag="cpu_baseline"):
-    """The FP64 oracle as it stands on the host cores: whole time steps of single
-    trajectories of the same workload, until about `seconds` of CPU work."""
+def _oracle_worker(job):
+    """One host process of the CPU baseline: whole W3 time steps of single
+    trajectories started from synthetic chi=64 states (the FP64 oracle as it
+    stands, single-threaded BLAS), for about `seconds`.  Returns (two-site
+    updates, seconds, trajectory steps)."""
+    seconds, worker, L, chi = job
     from oracle import tebd
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
     w = workloads.W3
     cfg = tebd.TrajectoryConfig(L, J=w["J"], dt=w["dt"], chi_max=chi, svd_cut=1e-12,
                                 gamma_loss=w["gamma_loss"], seed=w["seed"],
                                 occupation=workloads.occupation(L, "neel"))
     gates = tebd.StepGates(cfg)
-    updates = 0
-    n_traj = 0
+    updates, n = 0, 0
     t0 = time.perf_counter()
     while True:
-        B, lam, _ = workloads.synthetic_mps(L, chi, seed=1234 + n_traj % POOL)
+        tid = worker * 100003 + n
+        B, lam, _ = workloads.synthetic_mps(L, chi, seed=1234 + tid % POOL)
         tr = tebd.Trajectory.from_tensors(cfg, B, lam)
-        ch = tebd.step_trajectory(tr, gates, n_traj, 0)
+        ch = tebd.step_trajectory(tr, gates, tid, 0)
         if ch >= 0:
             site = ch // 3
             updates += max(site - 1, 0) + (L - 1)
         else:
             updates += sum(len(range(p, L - 1, 2)) for p, _ in cfg.layers())
-        n_traj += 1
+        n += 1
         if time.perf_counter() - t0 >= seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": updates / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
-            "sample": "%d W3 trajectories x 1 time step from synthetic chi=64 states "
-                      "(%d two-site updates, %.1f s)" % (n_traj, updates, dt)}
+    return updates, time.perf_counter() - t0, n
+
+
+def _spawn_pool_map(fn, jobs, workers):
+    """Run jobs in `workers` spawned processes with single-threaded BLAS (spawned,
+    not forked, so that no GPU context is inherited)."""
+    import multiprocessing as mp
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            return pool.map(fn, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu_baseline(seconds, L=64, chi=64, workers=None):
+    """The FP64 oracle as it stands on the host cores: one process per core,
+    each running whole time steps of its own W3 trajectories (the trajectories
+    are independent, so this is how the host parallelises), plus the same work
+    on a single core.  `seconds` bounds each of the two runs."""
+    workers = workers or os.cpu_count() or 1
+    one = _spawn_pool_map(_oracle_worker, [(seconds / 2, 0, L, chi)], 1)[0]
+    res = _spawn_pool_map(_oracle_worker, [(seconds, w, L, chi) for w in range(workers)], workers)
+    upd = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    n = sum(r[2] for r in res)
+    return {"value": upd / wall, "unit": UNIT, "cores": int(workers), "kind": "oracle",
+            "single_thread": one[0] / one[1],
+            "sample": "%d processes x W3 trajectories x 1 time step from synthetic chi=64 states "
+                      "(%d trajectory steps, %d two-site updates, %.1f s); single core: %d "
+                      "trajectory steps in %.1f s" % (workers, n, upd, wall, one[2], one[1])}
 
 
 def qsd_cpu_oracle(seconds, L, chi, dt, gamma_loss, gamma_deph):
@@ -329,6 +364,63 @@ def density_matrix_leg(lt, stream, args, alu_peak, method, L, chi, init, rates, 
                                                                  chi, rates, init)}
 
 
+def w3_full_run_leg(lt, stream, args):
+    """The W3 chain as configured (Neel start, ragged bond dimensions as the
+    physics makes them, 200 steps to T=4) in mixed precision: time to solution,
+    updates/s, per-step latency, and the ensemble C_ij at T=4 against the exact
+    untruncated histories of the same jump records (the Slater-determinant
+    reference, on the host, for the first `full_exact` trajectories)."""
+    import torch
+    from oracle import slater, tebd
+    w = workloads.W3
+    n, steps = args.full_traj, w["n_steps"]
+    ev = []
+    rec = []
+    with lt.Ensemble(w["L"], w["chi_max"], n, precision=lt.LT_MIXED, init="neel",
+                     stream=stream.cuda_stream, **w3_kwargs("mixed")) as e:
+        torch.cuda.synchronize()
+        e.counters(clear=True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s_ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rec.append(lt.lt_apply_jumps(e.ctx, s_, want_channels=True, n_traj=n))
+            for parity, tau in [(0, w["dt"] / 2), (1, w["dt"]), (0, w["dt"] / 2)]:
+                lt.lt_apply_layer(e.ctx, parity, tau)
+            b.record(stream)
+            ev.append((a, b))
+        t1.record(stream)
+        torch.cuda.synchronize()
+        tts = t0.elapsed_time(t1) / 1e3
+        cnt = e.counters()
+        _, dims = e.stats()
+        _, Cp = e.corr(per_traj=True)
+    rec = np.stack(rec, axis=1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ne = min(args.full_exact, n)
+    cfg = tebd.TrajectoryConfig(w["L"], J=w["J"], dt=w["dt"], chi_max=w["chi_max"], svd_cut=1e-6,
+                                gamma_loss=w["gamma_loss"], fermionic=True,
+                                occupation=workloads.occupation(w["L"], "neel"), seed=w["seed"])
+    exact = slater.run_slater(cfg, rec[:ne])
+    per = np.abs(Cp[:ne] - exact).reshape(ne, -1).max(1)
+    return {"workload": "W3 as configured: L=64, chi_max=64, %d trajectories from the Neel state, "
+                        "fermionic loss 0.2, dt=0.02, T=4 (200 steps), mixed precision, jumps "
+                        "sampled" % n,
+            "time_to_solution_s": tts, "updates_per_s": cnt["updates"] / tts,
+            "trajectory_steps_per_s": n * steps / tts,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "jumps": int((rec >= 0).sum()), "final_max_bond_dim": int(dims.max()),
+            "final_mean_bond_dim": float(dims.mean()),
+            "vs_exact_T4": {"trajectories": ne,
+                            "max_abs_corr_ensemble": float(np.abs(Cp[:ne].mean(0) - exact.mean(0)).max()),
+                            "max_abs_corr_per_traj_median": float(np.median(per)),
+                            "reference": "exact untruncated histories of the same jump records "
+                                         "(Slater determinants, host FP64)"}}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -384,6 +476,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     mps, packed = state_pool(L, chi, POOL)
     pk, src = peaks()
+    simt = lt.lt_pipe_peaks()   # measured FP32 (packed FMA) and FP64 pipe peaks
 
     def barrier():
         if world > 1:
@@ -447,6 +540,27 @@ def run_ours(args):
     cnt = ens.counters()
     hist = ens.sweep_histogram()
     launches = ens.launches() - launches0
+    # the same step replayed from a captured CUDA graph (lt_step_graph), after the
+    # timed region: the headline keeps plain launches so that every Trotter layer
+    # carries its own CUDA events for the roofline
+    graph = None
+    if args.graph_steps > 0:
+        try:
+            lt.lt_step_graph(ens.ctx, 1)      # capture + one replay
+            torch.cuda.synchronize()
+            ens.counters(clear=True)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            lt.lt_step_graph(ens.ctx, args.graph_steps)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            gs = g0.elapsed_time(g1) / 1e3
+            graph = {"steps": args.graph_steps, "updates_per_s": ens.counters()["updates"] / gs,
+                     "ms_per_step": 1e3 * gs / args.graph_steps,
+                     "note": "one captured step per replay (about 2L + 7 kernels); the "
+                             "headline uses plain launches, each layer timed by its own events"}
+        except Exception as err:
+            graph = {"error": repr(err)}
     step_ms = sorted(a.elapsed_time(b) for a, b in step_ev)
     layer_ms = [a.elapsed_time(b) for a, b in layer_ev]
     updates = cnt["updates"]
@@ -460,7 +574,8 @@ def run_ours(args):
     mean_layer_s = float(np.mean(layer_ms)) / 1e3
     flops_per_layer = cnt["layer_flops"] / max(len(layer_ms), 1)
     achieved = algorithmic_tflops(flops_per_layer, mean_layer_s)
-    alu_peak = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * FP32_LANES_PER_SM * 2 / 1e12
+    alu_peak = simt["fp32_tflops"]
+    alu_peak_derived = pk.get("sm_max_mhz", 2032.0) * 1e6 * 148 * FP32_LANES_PER_SM * 2 / 1e12
     sweeps_mean = float(np.sum(np.arange(64) * hist) / max(hist.sum(), 1))
     ens.close()
     del ens
@@ -485,8 +600,16 @@ def run_ours(args):
             b.record(stream)
             torch.cuda.synchronize()
             c64 = e64.counters()
-            fp64 = {"updates_per_s": c64["updates"] / (a.elapsed_time(b) / 1e3),
-                    "n_traj": n64, "steps": 1}
+            s64 = a.elapsed_time(b) / 1e3
+            tf64 = (c64["layer_flops"] + c64["sweep_flops"]) / s64 / 1e12
+            fp64 = {"updates_per_s": c64["updates"] / s64, "n_traj": n64, "steps": 1,
+                    "roofline": {"bound": "alu", "kernel": "bond_update_kernel<double>",
+                                 "achieved": tf64, "peak": simt["fp64_tflops"],
+                                 "unit": "TFLOP/s", "frac": tf64 / simt["fp64_tflops"],
+                                 "peak_source": "measured on this GPU (lt_pipe_peaks: "
+                                                "independent FP64 FMA chains)",
+                                 "note": "whole step (layers and re-canonicalisation) "
+                                         "over its wall time"}}
             e64.close()
     except Exception as err:  # recorded in the line; the headline still prints
         fp64 = {"error": repr(err)}
@@ -668,6 +791,14 @@ def run_ours(args):
     except Exception as err:  # recorded in the line; the headline still prints
         accuracy = {"error": repr(err)}
 
+    # ---- the configured W3 run to T = 4 from the Neel state --------------------------------
+    full = None
+    try:
+        if args.full_traj > 0 and solo:
+            full = w3_full_run_leg(lt, stream, args)
+    except Exception as err:  # recorded in the line; the headline still prints
+        full = {"error": repr(err)}
+
     # ---- end to end through the public API with host buffers ---------------------------
     e2e = None
     try:
@@ -740,8 +871,11 @@ def run_ours(args):
                                          "that capture (dram__bytes_read.sum + "
                                          "dram__bytes_write.sum of one Trotter-layer launch, "
                                          "4096 trajectories) gave 25.2 GB, 192 KB per update",
-                         "peak_source": "FP32 FMA lanes: 148 SM x 128 x 2 flop x sm_max_mhz "
-                                        "(%s clock)" % src,
+                         "peak_source": "measured on this GPU (lt_pipe_peaks: independent "
+                                        "packed FP32 FMA chains, 4 CTAs x 256 threads per SM, "
+                                        "CUDA events); derived from unit counts: %.1f TFLOP/s "
+                                        "(148 SM x 128 lanes x 2 flop x %s max clock)"
+                                        % (alu_peak_derived, src),
                          "mean_layer_ms": mean_layer_s * 1e3,
                          "flops_per_layer": flops_per_layer},
             "jacobi_sweeps_mean": sweeps_mean,
@@ -749,6 +883,8 @@ def run_ours(args):
             "speedup_vs_fp64": (value / world / fp64["updates_per_s"])
             if fp64 and "updates_per_s" in fp64 else None,
             "mixed_vs_fp64": accuracy,
+            "w3_to_T4": full,
+            "graph": graph,
             "qsd": qsd,
             "mpdo": mpdo_leg,
             "purified": purified_leg,

@@ -74,12 +74,16 @@ template <typename V, typename R> __device__ __forceinline__ V splat(R v) {
 // consecutive Bs words and share the broadcast Bl reads; for D = 4 a thread
 // takes one (a, c) and its 16 products.  Columns n..npad-1 are set to zero (the
 // Jacobi sweeps run over npad columns without tests), and so are the padding
-// rows D chiL .. mp-1.
+// rows D chiL .. mp-1.  Glo (single precision, or nullptr) holds the rounding
+// residual G - fl(G) of every gate entry: the gate is applied as fl(G) + Glo, so
+// the same rounding of the gate does not recur in every layer of every step (a
+// coherent error that the ensemble average would not remove), leaving only the
+// independent rounding of each accumulation.
 template <typename R, int D>
 __device__ void form_theta(R* Xr, R* Xi, int ldp, int npad, int mp, const typename CT<R>::T* Bl,
                            const typename CT<R>::T* Br, const typename CT<R>::T* Bs_in, int chiL,
-                           int chiM, int chiR, const typename CT<R>::T* G, const double* lamL,
-                           bool weighted) {
+                           int chiM, int chiR, const typename CT<R>::T* G,
+                           const typename CT<R>::T* Glo, const double* lamL, bool weighted) {
   typedef typename CT<R>::T Tc;
   const int n2 = D * chiR;
   if (npad > n2) {
@@ -127,6 +131,11 @@ __device__ void form_theta(R* Xr, R* Xi, int ldp, int npad, int mp, const typena
         for (int tp = 0; tp < D; ++tp) {
           const Tc* g = G + (sp * D + tp) * (D * D);
           Tc v = czero<Tc>();
+          if (Glo) {
+            const Tc* gl = Glo + (sp * D + tp) * (D * D);
+#pragma unroll
+            for (int u = 0; u < D * D; ++u) cfma(v, gl[u], p[u]);
+          }
 #pragma unroll
           for (int u = 0; u < D * D; ++u) cfma(v, g[u], p[u]);
           const int o = (D * a + sp) * ldp + tp * chiR + c;
@@ -173,6 +182,13 @@ __device__ void form_theta(R* Xr, R* Xi, int ldp, int npad, int mp, const typena
         for (int tp = 0; tp < 2; ++tp) {
           const Tc* g = G + (sp * 2 + tp) * 4;
           Tc v = czero<Tc>();
+          if (Glo) {
+            const Tc* gl = Glo + (sp * 2 + tp) * 4;
+            cfma(v, gl[0], p[u][0]);
+            cfma(v, gl[1], p[u][1]);
+            cfma(v, gl[2], p[u][2]);
+            cfma(v, gl[3], p[u][3]);
+          }
           cfma(v, g[0], p[u][0]);
           cfma(v, g[1], p[u][1]);
           cfma(v, g[2], p[u][2]);
@@ -1302,6 +1318,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
   __shared__ R s_nrm[LT_MAX_DIM];
   __shared__ int s_perm[LT_MAX_DIM];
   __shared__ Tc s_gate[D * D * D * D];
+  __shared__ Tc s_glo[D * D * D * D];  // gate rounding residual (single precision)
   __shared__ double s_lamL[LT_MAX_CHI];
   __shared__ int s_k, s_nrot;
   __shared__ double s_norm, s_wdisc;
@@ -1361,31 +1378,20 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     R* Xi = W + mcap * ldp;
     Tc* Y = reinterpret_cast<Tc*>(W + 2 * mcap * ldp);
     constexpr int D4 = D * D * D * D;
-    if constexpr (D4 <= 32) {
-      if (tid < D4) {
-        if (a.gates) {
-          const double2 g = a.gates[b * D4 + tid];
-          s_gate[tid] = cmk<Tc>(g.x, g.y);
-        } else {
-          s_gate[tid] = cmk<Tc>((tid % (D * D + 1)) == 0 ? 1.0 : 0.0, 0.0);
-        }
-      }
-    } else {
-      for (int i = tid; i < D4; i += blockDim.x) {
-        if (a.gates) {
-          const double2 g = a.gates[b * D4 + i];
-          s_gate[i] = cmk<Tc>(g.x, g.y);
-        } else {
-          s_gate[i] = cmk<Tc>((i % (D * D + 1)) == 0 ? 1.0 : 0.0, 0.0);
-        }
-      }
+    for (int i = tid; i < D4; i += blockDim.x) {
+      const double2 g = a.gates ? a.gates[b * D4 + i]
+                                : make_double2((i % (D * D + 1)) == 0 ? 1.0 : 0.0, 0.0);
+      const Tc h = cmk<Tc>(g.x, g.y);
+      s_gate[i] = h;
+      s_glo[i] = cmk<Tc>(g.x - (double)h.x, g.y - (double)h.y);
     }
     for (int i = tid; i < chiL; i += blockDim.x)
       s_lamL[i] = b == 0 ? 1.0 : a.lam[((long long)traj * (L - 1) + b - 1) * chi + i];
     if (tid == 0) s_nrot = 0;
     __syncthreads();
     if (mode == 0) {
-      form_theta<R, D>(Xr, Xi, ldp, npad, mpad, Bl, Br, Y, chiL, chiM, chiR, s_gate, s_lamL, true);
+      form_theta<R, D>(Xr, Xi, ldp, npad, mpad, Bl, Br, Y, chiL, chiM, chiR, s_gate,
+                       sizeof(R) == 4 ? s_glo : nullptr, s_lamL, true);
     } else {
       // one-site matrix, zero-padded to mpad x npad
       for (int i = tid; i < mpad * npad; i += blockDim.x) {
@@ -1534,8 +1540,8 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
       // B_b <- theta~ V_k (/ |S_k| in mode 0), B_{b+1} <- V_k^+
-      form_theta<R, D>(Xr, Xi, ldp, nJ, D * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate, s_lamL,
-                       false);
+      form_theta<R, D>(Xr, Xi, ldp, nJ, D * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate,
+                       sizeof(R) == 4 ? s_glo : nullptr, s_lamL, false);
       __syncthreads();
       const int m = D * chiL;
       const R invn = mode == 0 && !a.keep_norm ? (R)(1.0 / s_norm) : (R)1;
