@@ -446,12 +446,14 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-# DRAM bytes (read + write) of one Trotter-layer launch of bond_update_kernel<float>
-# on the 4096-trajectory workload from the last ncu capture
-# (profiles/launches_w3s_4096traj.md).  The kernel has changed since (templated on
-# the physical dimension, reflector phases from the scaled leading entry), so the
-# line reports traffic as null and this figure only as the last capture.
-LAYER_LAUNCH_DRAM_BYTES_LAST_CAPTURE = 12725311232 + 12486851584
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per two-site update of
+# bond_update_kernel<float, 2> in a Trotter-layer launch, from one ncu capture of the
+# three layer launches of a 256-trajectory case of the same workload (1.07 GB of site
+# tensors, larger than L2): 4.589 GB over 21,185 updates
+# (profiles/bond_update_kernel_dram_w3s_256traj.md).  Traffic grows in proportion to
+# the updates (every update reads and writes its two sites once), so a full launch is
+# this figure times its updates.
+BOND_DRAM_BYTES_PER_UPDATE = 4589290496 / 21185.0
 
 
 def algorithmic_tflops(flops, seconds):
@@ -864,20 +866,22 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "bond_update_kernel<float>",
                          "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak,
-                         "traffic": None,
-                         "traffic_last_capture": LAYER_LAUNCH_DRAM_BYTES_LAST_CAPTURE
-                         if n_traj == 4096 and world == 1 else None,
-                         "traffic_note": "null: the kernel changed after the last capture; "
-                                         "that capture (dram__bytes_read.sum + "
-                                         "dram__bytes_write.sum of one Trotter-layer launch, "
-                                         "4096 trajectories) gave 25.2 GB, 192 KB per update",
+                         "traffic": BOND_DRAM_BYTES_PER_UPDATE
+                         * cnt["layer_updates"] / max(len(layer_ms), 1),
+                         "traffic_note": "bytes per layer launch: DRAM bytes per update from "
+                                         "an ncu capture of the 256-trajectory case (%.0f B) "
+                                         "times this launch's updates; algorithmic %.0f B "
+                                         "(the two site tensors read and written once, "
+                                         "complex64)" % (BOND_DRAM_BYTES_PER_UPDATE,
+                                                         4 * 2 * chi * chi * 8),
                          "peak_source": "measured on this GPU (lt_pipe_peaks: independent "
                                         "packed FP32 FMA chains, 4 CTAs x 256 threads per SM, "
                                         "CUDA events); derived from unit counts: %.1f TFLOP/s "
                                         "(148 SM x 128 lanes x 2 flop x %s max clock)"
                                         % (alu_peak_derived, src),
                          "mean_layer_ms": mean_layer_s * 1e3,
-                         "flops_per_layer": flops_per_layer},
+                         "flops_per_layer": flops_per_layer,
+                         "updates_per_layer": cnt["layer_updates"] / max(len(layer_ms), 1)},
             "jacobi_sweeps_mean": sweeps_mean,
             "fp64_path": fp64,
             "speedup_vs_fp64": (value / world / fp64["updates_per_s"])

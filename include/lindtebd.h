@@ -53,8 +53,11 @@ typedef enum {
 
 typedef enum { LT_TRAJ = 0, LT_QSD = 1, LT_MPDO = 2, LT_PURIFIED = 3 } lt_method;
 
-/* LT_FP64: every step in double precision.  LT_MIXED: site tensors, theta and
- * the Jacobi rotations in single precision; singular values, the truncation
+/* LT_FP64: every step in double precision.  LT_MIXED: site tensors stored in
+ * single precision; theta formed on the tensor cores from exact products of 8-bit
+ * digits (pure states; the vectorised and purified forms in single precision) and
+ * rounded once; the Jacobi rotations in single precision, the kept right singular
+ * vectors re-orthonormalised with norms in double; singular values, the truncation
  * weight, the renormalisation, the Schmidt values Lambda and the jump
  * probabilities in double precision. */
 typedef enum { LT_FP64 = 0, LT_MIXED = 1 } lt_precision;
@@ -90,6 +93,10 @@ typedef struct {
   int64_t traj_offset;       /* global id of trajectory 0 (Philox counter word 0)  */
   double jacobi_tol;         /* rotate a row pair while |x.y^+| > tol |x| |y|;     */
                              /* 0 = default eps sqrt(n) of the working precision   */
+  int32_t theta_simt;        /* LT_MIXED with two values per site: 0 (default)     */
+                             /* forms theta on the tensor cores from exact 8-bit   */
+                             /* digit products (error below the final rounding);   */
+                             /* 1 forms it with single-precision FMAs              */
 } lt_config;
 
 /* Create a context: validate cfg, allocate the ensemble on the current device

@@ -295,6 +295,8 @@ lt_status check_device_error(lt_ctx_s* c) {
     return fail(c, LT_ERR_NUMERICAL, "jump decision", "jump probability per step >= 0.5; reduce dt");
   if (err & LT_EBIT_WORKSPACE)
     return fail(c, LT_ERR_NUMERICAL, "bond update", "a task exceeded its workspace");
+  if (err & LT_EBIT_TIMEOUT)
+    return fail(c, LT_ERR_TIMEOUT, "bond update", "a bounded wait on the tensor cores ran out");
   if (err & LT_EBIT_BADARG) {
     c->last_error = "replayed channel out of range";
     int zero = 0;
@@ -414,6 +416,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   c->cut = cfg->svd_cut;
   c->max_sweeps = cfg->max_sweeps > 0 ? cfg->max_sweeps : 40;
   c->jacobi_tol = cfg->jacobi_tol;
+  c->theta_tc = cfg->theta_simt ? 0 : 1;
   c->seed = cfg->seed;
   c->traj_offset = cfg->traj_offset;
   c->init = cfg->init;

@@ -26,6 +26,7 @@
 #define LT_EBIT_NOCONV 4       // Jacobi hit its sweep limit (recorded, not fatal)
 #define LT_EBIT_BADARG 8       // replayed channel out of range
 #define LT_EBIT_WORKSPACE 16   // a task did not fit its workspace (skipped)
+#define LT_EBIT_TIMEOUT 32     // a bounded wait on the tensor cores ran out (kernel returned)
 
 // ---- complex arithmetic on float2 / double2 ------------------------------------
 template <typename R> struct CT;
@@ -148,6 +149,7 @@ template <typename R> struct BondArgs {
   Tc* scratch;           // per-CTA workspace when it does not fit shared memory
   long long scratch_stride;
   int use_smem;
+  int use_tc;            // mode 0, single precision, D = 2: theta on the tensor cores
   int max_sweeps;
   double tol;            // Jacobi threshold, 0 = eps sqrt(n) of the working precision
   int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
@@ -236,6 +238,7 @@ struct lt_ctx_s {
   void* bond_scratch;
   long long bond_scratch_stride;
   int bond_grid, bond_use_smem;
+  int theta_tc;     // single precision, D = 2: theta on the tensor cores (digit products)
   size_t bond_smem;
 
   void* env_scratch;

@@ -19,6 +19,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "lt_internal.cuh"
 
 namespace {
@@ -1279,6 +1281,388 @@ __device__ void reorthonormalise_rows(float2* Y, int ld, int k, int n, float2* E
   }
 }
 
+
+// ---- theta on the tensor cores: exact products of 8-bit digits (single precision) --------
+// P = Bl Br (rows (a, s) of Bl, columns (t, c) of Br, inner index mu) is formed on the
+// 5th-generation tensor cores (tcgen05.mma, kind::f16 with bf16 operands, FP32
+// accumulators in tensor memory) without rounding: every single-precision value x of a
+// row of Bl (of a column of Br) is written as 2^e (d0 2^-7 + d1 2^-15 + d2 2^-23 + d3
+// 2^-31) + r, |r| <= 2^(e-32), with 2^e above the row's (column's) largest |Re|, |Im|
+// and signed integer digits |d| <= 128, which bf16 holds exactly.  A product of two
+// digits is an integer below 2^14, so the sum over mu <= 64 and over the (at most four)
+// digit pairs (i, j) of one order q = i + j, for Re = ArBr - AiBi and Im = ArBi + AiBr,
+// stays an integer below 2^23: each FP32 accumulator S_q is exact whatever order or
+// rounding mode the tensor core adds in.  The orders q = 0..3 are kept (the dropped
+// ones lie 2^-32 below the row-column scale), and P = 2^(e_r + f_c) sum_q S_q 2^(-14-8q)
+// is recombined as a pair of floats (two-sum of the two leading orders, the rest in the
+// low part).  The gate is then applied to that pair (its single-precision value and
+// residual, as in form_theta), so theta~ comes out rounded once.  Plain TF32 products
+// are not used here: their accumulation in the tensor core rounds toward zero, which
+// biases every contraction by a few 1e-7 in the same direction.
+namespace tcg {
+
+constexpr int TMEM_COLS = 512;   // 8 accumulators (S_0..S_3 of Re and Im) x 64 columns
+constexpr int TILE_N = 64;       // columns (t, c) per pass
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x
+// 16 bytes, `lbo` bytes between core matrices along K, `sbo` between 8-row groups
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;
+}
+// D[tmem] (+)= A B for M = 128, N = 64, K = 16, bf16 operands, FP32 accumulate
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_addr(bar)));
+}
+// wait for the phase `parity` of the barrier, at most 2^24 polls
+__device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity));
+  return done != 0;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+// 8 consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+// byte offset of (row, k) in a digit plane of `rows` rows (K-major, no swizzle)
+__device__ __forceinline__ int koff(int row, int k, int rows) {
+  return (k >> 3) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+// the four digits of x 2^-e (|x| < 2^e)
+__device__ __forceinline__ void digits(float x, int e, float* d) {
+  float v = ldexpf(x, 7 - e);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    d[t] = rintf(v);
+    v = (v - d[t]) * 256.f;
+  }
+}
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ int expo(float m) { return m > 0.f ? ilogbf(m) + 1 : -100; }
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// Bytes of shared memory the digit planes of one pass take for inner dimension <= kp
+__host__ __device__ constexpr int smem_bytes(int kp) { return 8 * 128 * kp * 2 + 8 * TILE_N * kp * 2; }
+
+}  // namespace tcg
+
+// Whether a mode-0 task of this shape takes the tensor-core theta: 2 chi_L and 2 chi_R
+// at most 128, chi_M at most 64, its digit planes within the workspace, and (with two
+// column passes) the first pass's theta~ within the slot of site b.
+__device__ __forceinline__ bool theta_tc_fits(int chiL, int chiM, int chiR, long long slot,
+                                              long long ws_bytes) {
+  const int kp = (chiM + 15) & ~15;
+  if (2 * chiL > 128 || 2 * chiR > 128 || chiM > 64) return false;
+  if ((long long)tcg::smem_bytes(kp) > ws_bytes) return false;
+  return 2 * chiR <= tcg::TILE_N || (long long)(2 * chiL) * tcg::TILE_N <= slot;
+}
+
+// theta~ = G (Bl Br) on the tensor cores, written over the site tensors of sites b and
+// b+1 (Bl, and the slot after it): pass T (columns n' = 2c + t in [64 T, 64 T + 64)) is
+// stored row-major with its own width at Bl + T slot, or, in one pass, across both
+// slots.  W: shared workspace (digit planes); s_er, s_fc: [128] exponents; tmem, bar,
+// phase: the CTA's tensor memory and barrier.  Returns false if a wait ran out.
+__device__ bool theta_tc(unsigned char* W, float2* Bl, const float2* Br, int chiL, int chiM,
+                         int chiR, long long slot, const float2* G, const float2* Glo,
+                         int* s_er, int* s_fc, uint32_t tmem, uint64_t* bar, uint32_t& phase) {
+  using namespace tcg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int m = 2 * chiL, n = 2 * chiR, kp = (chiM + 15) & ~15;
+  const int aplane = 128 * kp * 2, bplane = TILE_N * kp * 2;
+  unsigned char* A = W;
+  unsigned char* B = W + 8 * aplane;
+  // row exponents of Bl (rows (a, s)), column exponents of Br (columns n' = 2c + t)
+  for (int r = warp; r < 128; r += nw) {
+    float mx = 0.f;
+    if (r < m)
+      for (int k = lane; k < chiM; k += 32) {
+        const float2 v = Bl[(long long)r * chiM + k];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    if (lane == 0) s_er[r] = expo(mx);
+  }
+  for (int c2 = tid; c2 < n; c2 += blockDim.x) {
+    const int c = c2 >> 1, t = c2 & 1;
+    float mx = 0.f;
+    for (int k = 0; k < chiM; ++k) {
+      const float2 v = Br[(long long)k * n + t * chiR + c];
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    s_fc[c2] = expo(mx);
+  }
+  __syncthreads();
+  // A digit planes (Re digits 0..3, Im digits 0..3), 128 rows x kp, two k per thread step
+  for (int i = tid; i < 128 * (kp >> 1); i += blockDim.x) {
+    const int r = i / (kp >> 1), k = 2 * (i - r * (kp >> 1));
+    float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+    if (r < m) {
+      if (k < chiM) v0 = Bl[(long long)r * chiM + k];
+      if (k + 1 < chiM) v1 = Bl[(long long)r * chiM + k + 1];
+    }
+    float d0r[4], d1r[4], d0i[4], d1i[4];
+    const int e = s_er[r];
+    digits(v0.x, e, d0r);
+    digits(v1.x, e, d1r);
+    digits(v0.y, e, d0i);
+    digits(v1.y, e, d1i);
+    const int o = koff(r, k, 128);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      *reinterpret_cast<uint32_t*>(A + t * aplane + o) = pack2(d0r[t], d1r[t]);
+      *reinterpret_cast<uint32_t*>(A + (4 + t) * aplane + o) = pack2(d0i[t], d1i[t]);
+    }
+  }
+  const int passes = (n + TILE_N - 1) / TILE_N;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE_N >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  const uint32_t idesc_neg = idesc | (1u << 13);
+  bool ok = true;
+  for (int T = 0; T < passes && ok; ++T) {
+    const int n0 = T * TILE_N, nt = n - n0 < TILE_N ? n - n0 : TILE_N;
+    // B digit planes of this pass: row n' - n0 (column (t, c) of Br), inner index k
+    for (int i = tid; i < TILE_N * (kp >> 1); i += blockDim.x) {
+      const int nl = i % TILE_N, k = 2 * (i / TILE_N);
+      const int c2 = n0 + nl, c = c2 >> 1, t = c2 & 1;
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+      int e = -100;
+      if (nl < nt) {
+        e = s_fc[c2];
+        if (k < chiM) v0 = Br[(long long)k * n + t * chiR + c];
+        if (k + 1 < chiM) v1 = Br[(long long)(k + 1) * n + t * chiR + c];
+      }
+      float d0r[4], d1r[4], d0i[4], d1i[4];
+      digits(v0.x, e, d0r);
+      digits(v1.x, e, d1r);
+      digits(v0.y, e, d0i);
+      digits(v1.y, e, d1i);
+      const int o = koff(nl, k, TILE_N);
+#pragma unroll
+      for (int t4 = 0; t4 < 4; ++t4) {
+        *reinterpret_cast<uint32_t*>(B + t4 * bplane + o) = pack2(d0r[t4], d1r[t4]);
+        *reinterpret_cast<uint32_t*>(B + (4 + t4) * bplane + o) = pack2(d0i[t4], d1i[t4]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+      const uint32_t a0 = smem_addr(A), b0 = smem_addr(B);
+      for (int ks = 0; ks < kp / 16; ++ks)
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j + i < 4; ++j) {
+            const int q = i + j;
+            const uint32_t acc = (ks > 0 || i > 0) ? 1u : 0u;  // (0, q) opens S_q
+            const uint32_t dre = tmem + q * TILE_N, dim = tmem + (4 + q) * TILE_N;
+            const uint64_t ar = sdesc(a0 + i * aplane + ks * 2 * 128 * 16, 128 * 16, 128);
+            const uint64_t ai = sdesc(a0 + (4 + i) * aplane + ks * 2 * 128 * 16, 128 * 16, 128);
+            const uint64_t br = sdesc(b0 + j * bplane + ks * 2 * TILE_N * 16, TILE_N * 16, 128);
+            const uint64_t bi = sdesc(b0 + (4 + j) * bplane + ks * 2 * TILE_N * 16, TILE_N * 16, 128);
+            mma(dre, ar, br, idesc, acc);
+            mma(dre, ai, bi, idesc_neg, 1u);
+            mma(dim, ar, bi, idesc, acc);
+            mma(dim, ai, br, idesc, 1u);
+          }
+      commit(bar);
+    }
+    // block-uniform outcome: every thread takes the same path through the epilogue
+    ok = __syncthreads_and(wait(bar, phase) ? 1 : 0) != 0;
+    phase ^= 1u;
+    fence_after();
+    if (ok) {
+      // epilogue: warp (quadrant, column group); lane = row (a, s) of the accumulators
+      const int row = 32 * (warp & 3) + lane, cg = warp >> 2;
+      const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+      const int width = passes == 1 ? n : nt;
+      float2* out = Bl + (passes == 1 ? 0 : (long long)T * slot);
+      for (int h = 0; h < (TILE_N / 8) / (nw / 4); ++h) {
+        const int col0 = 8 * (cg + (nw / 4) * h);  // 8 columns n' - n0 = 4 values of c
+        float S[8][8];
+#pragma unroll
+        for (int acc = 0; acc < 8; ++acc) ld8(tl + acc * TILE_N + col0, S[acc]);
+        // P = 2^(e_r + f_c) sum_q S_q 2^(-14 - 8q) as hi + lo, Re and Im
+        float ph[8][2], pl[8][2];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c2 = n0 + col0 + j;
+          const int e = s_er[row] + (c2 < n ? s_fc[c2] : 0);
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            const float* q = &S[4 * part][0];
+            float hi, lo;
+            two_sum(ldexpf(q[0 * 8 + j], -14), ldexpf(q[1 * 8 + j], -22), hi, lo);
+            lo += ldexpf(q[2 * 8 + j], -30) + ldexpf(q[3 * 8 + j], -38);
+            ph[j][part] = ldexpf(hi, e);
+            pl[j][part] = ldexpf(lo, e);
+          }
+        }
+        // gate on (s, t): the partner row (a, 1 - s) is the neighbouring lane
+        const int s = row & 1;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          float2 Ph[4], Pl[4];  // index u = 2 s2 + t2
+#pragma unroll
+          for (int t2 = 0; t2 < 2; ++t2) {
+            const int j = 2 * cc + t2;
+            const float oh0 = __shfl_xor_sync(FULL, ph[j][0], 1), oh1 = __shfl_xor_sync(FULL, ph[j][1], 1);
+            const float ol0 = __shfl_xor_sync(FULL, pl[j][0], 1), ol1 = __shfl_xor_sync(FULL, pl[j][1], 1);
+            Ph[2 * s + t2] = make_float2(ph[j][0], ph[j][1]);
+            Pl[2 * s + t2] = make_float2(pl[j][0], pl[j][1]);
+            Ph[2 * (1 - s) + t2] = make_float2(oh0, oh1);
+            Pl[2 * (1 - s) + t2] = make_float2(ol0, ol1);
+          }
+          const int c = (n0 + col0) / 2 + cc;
+          if (row < m && c < chiR) {
+#pragma unroll
+            for (int tp = 0; tp < 2; ++tp) {
+              const float2* g = G + (s * 2 + tp) * 4;
+              const float2* gl = Glo + (s * 2 + tp) * 4;
+              float2 hi = make_float2(0.f, 0.f), lo = hi;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                cfma(hi, g[u], Ph[u]);
+                cfma(lo, g[u], Pl[u]);
+                cfma(lo, gl[u], Ph[u]);
+              }
+              out[(long long)row * width + (2 * c + tp - n0)] = make_float2(hi.x + lo.x, hi.y + lo.y);
+            }
+          }
+        }
+      }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+  return ok;
+}
+
+// theta~ (in the layout theta_tc wrote) into the planes, times w_a when weighted; zero
+// padding to mp rows and npad columns as form_theta leaves it
+__device__ void theta_tc_planes(float* Xr, float* Xi, int ldp, int npad, int mp, const float2* Bl,
+                                int chiL, int chiR, long long slot, const double* lamL,
+                                bool weighted) {
+  const int m = 2 * chiL, n = 2 * chiR;
+  const int passes = (n + tcg::TILE_N - 1) / tcg::TILE_N;
+  for (int i = threadIdx.x; i < mp * npad; i += blockDim.x) {
+    const int r = i / npad, col = i - r * npad;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < m && col < n) {
+      const int tp = col / chiR, c = col - tp * chiR, c2 = 2 * c + tp;
+      const int T = passes == 1 ? 0 : c2 / tcg::TILE_N;
+      const int width = passes == 1 ? n : (n - T * tcg::TILE_N < tcg::TILE_N ? n - T * tcg::TILE_N
+                                                                               : tcg::TILE_N);
+      v = Bl[(long long)T * slot + (long long)r * width + (c2 - T * tcg::TILE_N)];
+      if (weighted) {
+        const float w = (float)lamL[r >> 1];
+        v.x *= w;
+        v.y *= w;
+      }
+    }
+    Xr[r * ldp + col] = v.x;
+    Xi[r * ldp + col] = v.y;
+  }
+}
+
+
+// Tensor-core pass of a Trotter layer (single precision, two values per site): for every
+// (trajectory, bond) task of the layer whose shape fits (theta_tc_fits, the same test
+// the bond kernel makes), theta~ = G (B_b B_{b+1}) replaces the two site tensors in the
+// layout theta_tc describes; the bond kernel then reads it instead of forming theta.
+// One CTA per SM (the digit planes take up to 192 KB of shared memory), each holding 512
+// columns of tensor memory and one barrier for the whole launch.
+__global__ void __launch_bounds__(512, 1) theta_tc_kernel(BondArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_er[128], s_fc[128];
+  __shared__ float2 s_gate[16], s_glo[16];
+  const int tid = threadIdx.x, L = a.L;
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tcg::smem_addr(&s_tmem)),
+                 "r"(tcg::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tcg::smem_addr(&s_bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  uint32_t phase = 0;
+  bool ok = true;
+  const long long ntask = (long long)(*a.n_trajs) * a.nb;
+  const long long ws_bytes = a.ws_elems * (long long)sizeof(float2);
+  for (long long task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+    const int traj = a.trajs[task / a.nb];
+    const int b = a.bond0 + 2 * (int)(task % a.nb);
+    const int* dm = a.dims + (long long)traj * (L - 1);
+    const int chiL = b == 0 ? 1 : dm[b - 1];
+    const int chiM = dm[b];
+    const int chiR = b == L - 2 ? 1 : dm[b + 1];
+    if (!theta_tc_fits(chiL, chiM, chiR, a.slot, ws_bytes)) continue;
+    if (tid < 16) {
+      const double2 g = a.gates[b * 16 + tid];
+      const float2 h = make_float2((float)g.x, (float)g.y);
+      s_gate[tid] = h;
+      s_glo[tid] = make_float2((float)(g.x - (double)h.x), (float)(g.y - (double)h.y));
+    }
+    __syncthreads();
+    float2* Bl = a.B + ((long long)traj * L + b) * a.slot;
+    ok = theta_tc(smem_raw, Bl, Bl + a.slot, chiL, chiM, chiR, a.slot, s_gate, s_glo, s_er, s_fc,
+                  s_tmem, &s_bar, phase);
+    if (!ok && tid == 0) atomicOr(a.err, LT_EBIT_TIMEOUT);
+  }
+  // after a wait that ran out, give the outstanding products one more bounded wait
+  // before the tensor memory is released
+  if (!ok) tcg::wait(&s_bar, phase ^ 1u);
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  if (tid < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem),
+                 "r"(tcg::TMEM_COLS));
+}
+
 // ---- the two-site update and the one-site canonical-form steps -----------------------------
 // mode 0: two-site update with the layer's gate (Eq. Theta): theta = Lambda_{b-1}
 //         G (B_b B_{b+1}), SVD, keep k, Lambda_b = S_k/|S_k|, B_{b+1} = V_k^+,
@@ -1329,6 +1713,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
                     : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
   const int L = a.L, chi = a.chi, tid = threadIdx.x, mode = a.mode;
   const long long ntask = (long long)(*a.n_trajs) * a.nb;
+  // theta~ formed beforehand on the tensor cores (theta_tc_kernel) for the mode-0 tasks
+  // that fit, left over the two site slots
+  constexpr bool kTc = sizeof(R) == 4 && D == 2;
+  const bool use_tc = kTc && a.use_tc && a.use_smem;
   for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
     const int traj = a.trajs[task / a.nb];
     const int b = a.bond0 + 2 * (int)(task % a.nb);
@@ -1389,7 +1777,17 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       s_lamL[i] = b == 0 ? 1.0 : a.lam[((long long)traj * (L - 1) + b - 1) * chi + i];
     if (tid == 0) s_nrot = 0;
     __syncthreads();
-    if (mode == 0) {
+    bool tc_task = false;
+    if constexpr (kTc) {
+      tc_task = use_tc && mode == 0 &&
+                theta_tc_fits(chiL, chiM, chiR, a.slot, a.ws_elems * (long long)sizeof(Tc));
+    }
+    if (tc_task) {
+      if constexpr (kTc)
+        theta_tc_planes(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, npad,
+                        mpad, reinterpret_cast<const float2*>(Bl), chiL, chiR, a.slot, s_lamL,
+                        true);
+    } else if (mode == 0) {
       form_theta<R, D>(Xr, Xi, ldp, npad, mpad, Bl, Br, Y, chiL, chiM, chiR, s_gate,
                        sizeof(R) == 4 ? s_glo : nullptr, s_lamL, true);
     } else {
@@ -1540,8 +1938,16 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     if (mode != 2) {
       // theta~ = G (B_b B_{b+1}) (identity gate in mode 1), then
       // B_b <- theta~ V_k (/ |S_k| in mode 0), B_{b+1} <- V_k^+
-      form_theta<R, D>(Xr, Xi, ldp, nJ, D * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate,
-                       sizeof(R) == 4 ? s_glo : nullptr, s_lamL, false);
+      if (tc_task) {
+        // theta~ as the tensor-core pass left it over the two site slots
+        if constexpr (kTc)
+          theta_tc_planes(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, nJ,
+                          D * chiL, reinterpret_cast<const float2*>(Bl), chiL, chiR, a.slot,
+                          s_lamL, false);
+      } else {
+        form_theta<R, D>(Xr, Xi, ldp, nJ, D * chiL, Bl, Br, nullptr, chiL, chiM, chiR, s_gate,
+                         sizeof(R) == 4 ? s_glo : nullptr, s_lamL, false);
+      }
       __syncthreads();
       const int m = D * chiL;
       const R invn = mode == 0 && !a.keep_norm ? (R)(1.0 / s_norm) : (R)1;
@@ -2749,7 +3155,14 @@ size_t bond_smem_bytes(int chi, size_t celt, int d) {
       mp_of(c2, c1) * (npad_of(c2, c1) + 2) + mx(c1 * (c1 + 1) + c1 * c2, refl(c1, c1));
   size_t need = need0 > need1 ? need0 : need1;
   need = need > need2 ? need : need2;
-  return need * celt;
+  size_t bytes = need * celt;
+  if (single && d == 2) {
+    // digit planes of the tensor-core theta (inner dimension up to 64)
+    const int kp = ((chi < 64 ? chi : 64) + 15) & ~15;
+    const size_t tc = (size_t)tcg::smem_bytes(kp);
+    if (tc > bytes) bytes = tc;
+  }
+  return bytes;
 }
 
 size_t env_scratch_elems(int L, int chi) { return ((size_t)L + 1 + 7) * (size_t)chi * chi; }
@@ -2786,6 +3199,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.scratch = reinterpret_cast<typename CT<R>::T*>(c->bond_scratch);
   a.scratch_stride = c->bond_scratch_stride;
   a.use_smem = c->bond_use_smem;
+  a.use_tc = sizeof(R) == 4 && D == 2 && mode == 0 && c->bond_use_smem && c->theta_tc;
   a.max_sweeps = c->max_sweeps;
   a.tol = c->jacobi_tol;
   a.sweep_hist = c->sweep_hist;
@@ -2793,6 +3207,15 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.keep_norm = (c->method == LT_QSD || c->method == LT_PURIFIED) && mode == 0;
   a.logw = c->method == LT_QSD && mode == 2 ? c->logw : nullptr;
   a.multiplet = c->method == LT_MPDO ? (c->prec == LT_MIXED ? 1e-5 : 1e-9) : 0.0;
+  if constexpr (sizeof(R) == 4 && D == 2) {
+    if (a.use_tc) {
+      const int kp = ((c->chi < 64 ? c->chi : 64) + 15) & ~15;
+      theta_tc_kernel<<<c->num_sms, 512, tcg::smem_bytes(kp), c->stream>>>(a);
+      c->launches++;
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
   bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0,
                              c->stream>>>(a);
   c->launches++;
@@ -3048,6 +3471,11 @@ cudaError_t configure_bond(lt_ctx_s* c) {
     e = c->prec == LT_MIXED ? bond_attributes<float, 2>(limit, c->bond_smem, &occ)
                             : bond_attributes<double, 2>(limit, c->bond_smem, &occ);
   if (e != cudaSuccess) return e;
+  if (c->prec == LT_MIXED && c->d == 2) {
+    e = cudaFuncSetAttribute(theta_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tcg::smem_bytes(64));
+    if (e != cudaSuccess) return e;
+  }
   if (occ < 1) occ = 1;
   c->bond_grid = occ * c->num_sms;
   c->bond_scratch_stride = c->bond_use_smem ? 0 : (long long)(need / c->celt);

@@ -28,9 +28,10 @@ def test_library_exports_every_declared_symbol():
 
 def test_config_struct_layout_matches_header():
     from paper_2609_18841_b300.lindtebd import lt_config
-    assert ctypes.sizeof(lt_config) == 120
+    assert ctypes.sizeof(lt_config) == 128
     assert lt_config.J.offset == 40 and lt_config.svd_cut.offset == 88
     assert lt_config.traj_offset.offset == 104 and lt_config.jacobi_tol.offset == 112
+    assert lt_config.theta_simt.offset == 120
 
 
 @pytest.mark.parametrize("kw,status", [
