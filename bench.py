@@ -50,12 +50,14 @@ def parse():
     ap.add_argument("--qsd-steps", type=int, default=2)
     ap.add_argument("--qsd-chi128-traj", type=int, default=64)
     ap.add_argument("--mpdo-steps", type=int, default=250)
-    ap.add_argument("--mpdo-sat-steps", type=int, default=3)
+    ap.add_argument("--mpdo-sat-steps", type=int, default=2)
+    ap.add_argument("--dm-cap-s", type=float, default=45.0)
     ap.add_argument("--mpdo-acc-steps", type=int, default=20)
     ap.add_argument("--mpdo-batch", type=int, default=148)
     ap.add_argument("--purified-steps", type=int, default=50)
-    ap.add_argument("--serve-requests", type=int, default=40)
-    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-cap-s", type=float, default=90.0)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--acc-steps", type=int, default=2)
     ap.add_argument("--full-traj", type=int, default=512)
@@ -317,8 +319,15 @@ def density_matrix_leg(lt, stream, args, alu_peak, method, L, chi, init, rates, 
         torch.cuda.synchronize()
         return ev[0].elapsed_time(ev[1]) / 1e3, e.counters()
 
+    # time to solution, in chunks of 10 steps, stopped at args.dm_cap_s of device time
     with lt.Ensemble(L, chi, 1, precision=lt.LT_MIXED, svd_cut=1e-6, **kw) as e:
-        s_tts, c_tts = timed(e, steps)
+        s_tts, done, c_tts = 0.0, 0, {"layer_updates": 0}
+        while done < steps and s_tts < args.dm_cap_s:
+            n = min(10, steps - done)
+            s_, c_ = timed(e, n)
+            s_tts += s_
+            c_tts["layer_updates"] += c_["layer_updates"]
+            done += n
         n_end = e.density()[0]
         _, dims_end = e.stats()
     sat = {}
@@ -355,7 +364,9 @@ def density_matrix_leg(lt, stream, args, alu_peak, method, L, chi, init, rates, 
                  "alu_frac": c_b["layer_flops"] / s_b / 1e12 / alu_peak}
     return {"workload": workload,
             "time_to_solution": {"T": steps * rates["dt"], "steps": steps, "precision": "mixed",
-                                 "s": s_tts, "ms_per_step": 1e3 * s_tts / steps,
+                                 "steps_done": done, "T_reached": done * rates["dt"],
+                                 "stopped_at_cap": done < steps, "cap_s": args.dm_cap_s,
+                                 "s": s_tts, "ms_per_step": 1e3 * s_tts / max(done, 1),
                                  "updates_per_s": c_tts["layer_updates"] / s_tts,
                                  "final_max_bond_dim": int(dims_end.max()),
                                  "final_density_range": [float(n_end.min()), float(n_end.max())]},
@@ -419,6 +430,82 @@ def w3_full_run_leg(lt, stream, args):
                             "max_abs_corr_per_traj_median": float(np.median(per)),
                             "reference": "exact untruncated histories of the same jump records "
                                          "(Slater determinants, host FP64)"}}
+
+
+def serving_leg(lt, args):
+    """The serving configuration: a Poisson stream at `serve_rate` requests/s, each
+    drawing the method (trajectory, QSD, MPDO, purified), L uniform in 16..128, chi_max
+    in {32, 64, 128, 256} ({32, 64, 128} for the density matrices, whose theta is 4 chi
+    wide), 1..512 trajectories (a power of two; 1..8 chains for the density matrices)
+    and T uniform in [1, 5] at dt = 0.02, admitted by device footprint.  The run stops
+    at `serve_cap_s` of wall time; requests unfinished by then are reported as such."""
+    rng = np.random.default_rng(77)
+    n_req, rate, cap = args.serve_requests, args.serve_rate, args.serve_cap_s
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    methods = (lt.LT_TRAJ, lt.LT_QSD, lt.LT_MPDO, lt.LT_PURIFIED)
+    reqs = []
+    for i in range(n_req):
+        method = methods[int(rng.integers(4))]
+        dm = method in (lt.LT_MPDO, lt.LT_PURIFIED)
+        T = float(rng.uniform(1.0, 5.0))
+        kw = dict(n_steps=int(round(T / 0.02)), L=int(rng.integers(16, 129)),
+                  chi_max=int(rng.choice([32, 64, 128] if dm else [32, 64, 128, 256])),
+                  n_traj=int(2 ** rng.integers(0, 4 if dm else 10)),
+                  precision=lt.LT_MIXED, method=method, dt=0.02, seed=100 + i, svd_cut=1e-6,
+                  init="neel")
+        if method == lt.LT_TRAJ:
+            kw.update(gamma_loss=0.1)
+        elif method == lt.LT_QSD:
+            kw.update(gamma_deph=0.1, gamma_loss=0.05, fermionic_jumps=0)
+        else:
+            kw.update(gamma_loss=0.1, gamma_gain=0.05, gamma_deph=0.02, fermionic_jumps=0)
+            if method == lt.LT_PURIFIED:
+                kw["kraus_dim"] = 2
+        reqs.append(kw)
+    failed, lat, upd, done_ids = {}, [], 0, set()
+    with lt.Server(args.serve_budget_gb << 30, 64) as srv:
+        ids, k = [], 0
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            while k < n_req and arrivals[k] <= now:
+                ids.append(srv.submit(**reqs[k]))
+                k += 1
+            q, a, _ = srv.tick()
+            if k == n_req and q == 0 and a == 0:
+                break
+            if now > cap and k == n_req:
+                break
+            if q == 0 and a == 0:
+                time.sleep(max(0.0, min(0.002, arrivals[k] - now)))
+        wall = time.perf_counter() - t0
+        for rid in ids:
+            try:
+                st, _, _, t = srv.result(rid)
+            except Exception:
+                continue
+            if st == lt.LT_ERR_STATE:
+                continue
+            done_ids.add(rid)
+            if st == lt.LT_OK:
+                lat.append(t[2] - t[0])
+                upd += srv.updates(rid)
+            else:
+                failed[str(rid)] = srv.error(rid) or "status %d" % st
+    unfinished = n_req - len(done_ids)
+    return {"requests": n_req, "completed": len(lat), "failed": failed,
+            "unfinished_at_cap": unfinished, "cap_s": cap, "arrival_rate_per_s": rate,
+            "wall_s": wall, "completed_per_s": len(lat) / wall,
+            "updates_per_s_completed": upd / wall,
+            "latency_s": {"p50": float(np.percentile(lat, 50)),
+                          "p99": float(np.percentile(lat, 99))} if lat else None,
+            "mix": "Poisson arrivals at %g/s; method trajectory, QSD, MPDO or purified "
+                   "(1:1:1:1); L uniform in 16..128; chi_max in {32,64,128,256} (density "
+                   "matrices {32,64,128}); 1..512 trajectories (powers of two; density "
+                   "matrices 1..8 chains); T uniform in [1,5] at dt=0.02; mixed precision; "
+                   "Neel start; admitted by device footprint; latency from submission to "
+                   "completion" % rate,
+            "budget_gb": args.serve_budget_gb}
 
 
 def run_reference(args):
@@ -679,82 +766,27 @@ def run_ours(args):
     try:
         if args.mpdo_steps > 0 and solo:
             mpdo_leg = density_matrix_leg(
-                lt, stream, args, alu_peak, method=lt.LT_MPDO, L=32, chi=64, init="domain_wall",
+                lt, stream, args, alu_peak, method=lt.LT_MPDO, L=32, chi=128, init="domain_wall",
                 rates=dict(dt=0.02, gamma_loss=0.1, gamma_gain=0.05), steps=args.mpdo_steps,
                 workload="MPDO (d^2 = 4): L=32 XX chain, spin loss 0.1 and gain 0.05 on every site, "
-                         "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=64 (theta up to "
-                         "256 x 256, the library's limit; chi_max = 128 would need 512 x 512)")
+                         "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=128 (theta up to "
+                         "512 x 512)")
         if args.purified_steps > 0 and solo:
             purified_leg = density_matrix_leg(
-                lt, stream, args, alu_peak, method=lt.LT_PURIFIED, L=64, chi=64, init="neel",
+                lt, stream, args, alu_peak, method=lt.LT_PURIFIED, L=64, chi=96, init="neel",
                 rates=dict(dt=0.01, gamma_loss=0.05, gamma_deph=0.1), steps=args.purified_steps,
                 workload="purified rho = X X^+ (physical d = 2, Kraus dimension 2): L=64 XX chain, "
                          "dephasing 0.1 and spin loss 0.05 on every site, dt=0.01, 2nd-order Trotter "
-                         "then the R step, Neel start, chi_max=64 (theta up to 256 x 256, the "
-                         "library's limit; chi_max = 96 would need 384 x 384)")
+                         "then the R step, Neel start, chi_max=96 (theta up to 384 x 384)")
     except Exception as err:  # recorded in the line; the headline still prints
         mpdo_leg = {"error": repr(err)}
         purified_leg = {"error": repr(err)}
 
-    # ---- serving: Poisson arrivals of mixed requests through the request server --------
+    # ---- serving: the configured request mix (Poisson arrivals) through the server ------
     serving = None
     try:
         if args.serve_requests > 0 and solo:
-            rng = np.random.default_rng(77)
-            n_req, rate = args.serve_requests, args.serve_rate
-            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
-            reqs = []
-            methods = (lt.LT_TRAJ, lt.LT_QSD, lt.LT_MPDO, lt.LT_PURIFIED)
-            for i in range(n_req):
-                method = methods[int(rng.integers(4))]
-                dm = method in (lt.LT_MPDO, lt.LT_PURIFIED)
-                kw = dict(n_steps=int(rng.integers(10, 31)), L=int(rng.choice([16, 32, 64, 128])),
-                          chi_max=int(rng.choice([32, 64] if dm else [32, 64, 128])),
-                          n_traj=int(rng.choice([1, 2, 4] if dm else [1, 8, 32, 128])),
-                          precision=lt.LT_MIXED, method=method, dt=0.02, seed=100 + i, svd_cut=1e-6,
-                          init="neel")
-                if method == lt.LT_TRAJ:
-                    kw.update(gamma_loss=0.1)
-                elif method == lt.LT_QSD:
-                    kw.update(gamma_deph=0.1, gamma_loss=0.05, fermionic_jumps=0)
-                else:
-                    kw.update(gamma_loss=0.1, gamma_gain=0.05, gamma_deph=0.02, fermionic_jumps=0)
-                    if method == lt.LT_PURIFIED:
-                        kw["kraus_dim"] = 2
-                reqs.append(kw)
-            failed = {}
-            with lt.Server(args.serve_budget_gb << 30, 64) as srv:
-                ids, k = [], 0
-                t0 = time.perf_counter()
-                while True:
-                    now = time.perf_counter() - t0
-                    while k < n_req and arrivals[k] <= now:
-                        ids.append(srv.submit(**reqs[k]))
-                        k += 1
-                    q, a, _ = srv.tick()
-                    if k == n_req and q == 0 and a == 0:
-                        break
-                    if q == 0 and a == 0:
-                        time.sleep(max(0.0, min(0.002, arrivals[k] - now)))
-                wall = time.perf_counter() - t0
-                lat = []
-                for rid in ids:
-                    st, _, _, t = srv.result(rid)
-                    if st == lt.LT_OK:
-                        lat.append(t[2] - t[0])
-                    else:
-                        failed[str(rid)] = srv.error(rid) or "status %d" % st
-            serving = {"requests": n_req, "completed": len(lat), "failed": failed,
-                       "arrival_rate_per_s": rate, "wall_s": wall,
-                       "completed_per_s": len(lat) / wall,
-                       "latency_s": {"p50": float(np.percentile(lat, 50)),
-                                     "p99": float(np.percentile(lat, 99))} if lat else None,
-                       "mix": "trajectory, QSD, MPDO or purified (1:1:1:1), L in {16,32,64,128}, "
-                              "chi_max in {32,64,128} (density matrices {32,64}), 1..128 "
-                              "trajectories (density matrices 1..4 chains), 10..30 steps of "
-                              "dt=0.02, mixed precision, Neel start; Poisson arrivals; latency from "
-                              "submission to completion",
-                       "budget_gb": args.serve_budget_gb}
+            serving = serving_leg(lt, args)
     except Exception as err:  # recorded in the line; the headline still prints
         serving = {"error": repr(err)}
 

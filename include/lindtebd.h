@@ -71,7 +71,7 @@ typedef enum {
 
 typedef struct {
   int32_t L;                 /* chain length, 2 <= L <= 1024                       */
-  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 128 (<= 64 for */
+  int32_t chi_max;           /* bond-dimension cap, 1 <= chi_max <= 256 (<= 128 for*/
                              /* LT_MPDO and LT_PURIFIED, whose theta is 4 chi wide)*/
   int32_t n_traj;            /* trajectories held by this context, >= 1            */
   int32_t kraus_dim;         /* LT_PURIFIED: Kraus dimension, 2 (0 selects 2); set */
@@ -104,7 +104,7 @@ typedef struct {
  * initial pure state is an eigenvector of rho(0), here a product state); an
  * LT_MPDO chain starts from rho = |n><n| of that product state (local index
  * 3 n_i on every site), an LT_PURIFIED chain from X = |n> with Kraus index 0
- * (s = 2 n_i).  LT_ERR_UNSUPPORTED: LT_MPDO or LT_PURIFIED with chi_max > 64,
+ * (s = 2 n_i).  LT_ERR_UNSUPPORTED: LT_MPDO or LT_PURIFIED with chi_max > 128,
  * LT_PURIFIED with kraus_dim other than 0 or 2, either with fermionic loss or
  * gain on a bulk site (on the chain
  * ends the Jordan-Wigner string acts as the total parity, which commutes with
@@ -317,6 +317,10 @@ lt_status lt_server_tick(lt_server server, int32_t* n_queued, int32_t* n_active,
  * it failed (times are still written). */
 lt_status lt_server_result(lt_server server, int64_t id, double* mean, double* sem,
                            double* times);
+/* Two-site updates a finished request executed (its context's work counter,
+ * lt_get_counters out[0], read at retirement; 0 if it failed).  LT_ERR_STATE while
+ * it runs. */
+lt_status lt_server_updates(lt_server server, int64_t id, uint64_t* updates);
 /* Why a finished request failed (the failing call and the CUDA message), "" if
  * it succeeded or is unknown; valid until the server is destroyed. */
 const char* lt_server_error(lt_server server, int64_t id);

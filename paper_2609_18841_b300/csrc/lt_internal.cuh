@@ -9,8 +9,8 @@
 
 #include "lindtebd.h"
 
-#define LT_MAX_CHI 128
-#define LT_MAX_DIM (2 * LT_MAX_CHI)  // largest theta side, d * chi_max
+#define LT_MAX_CHI 256
+#define LT_MAX_DIM 512  // largest theta side: 2 chi_max for pure states, 4 chi_max (<= 128) otherwise
 // the single-precision register paths of the two-site update (row-resident
 // Householder steps, blocked Jacobi, V_k^+ assembly) cover theta sides up to
 // LT_REG_DIM and up to LT_REG_CHI kept values; larger tasks take the

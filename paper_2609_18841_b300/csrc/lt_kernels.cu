@@ -284,7 +284,7 @@ __device__ __forceinline__ int jacobi_span(int n) {
   return gs;
 }
 
-template <typename R, int EPP>
+template <typename R, int EPP, bool CHUNKED>
 __device__ int jacobi_rows(R* Xr, R* Xi, int ldp, int m, int n, R* nrm, int* nrot, int max_sweeps,
                            double tol_override) {
   typedef typename CT<R>::T V;  // a pair of reals of one plane
@@ -293,6 +293,9 @@ __device__ int jacobi_rows(R* Xr, R* Xi, int ldp, int m, int n, R* nrm, int* nro
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int npairs = m / 2;
   const int iters = (npairs + ng - 1) / ng;
+  // rows longer than one group's span (2 EPP 32 columns) are handled in chunks of it:
+  // the inner product accumulates over the chunks, the rotation reloads them
+  const int span = 2 * EPP * gs, nch = CHUNKED ? (n + span - 1) / span : 1;
   const bool remap = gs == 8 && ng == 64 && npairs == 64;
   const R tol = tol_override > 0.0 ? (R)tol_override : Eps<R>::v * sqrt((R)n);
   // partner rows of this group's pair in round 0; when every pair of a round
@@ -326,22 +329,25 @@ __device__ int jacobi_rows(R* Xr, R* Xi, int ldp, int m, int n, R* nrm, int* nro
         R gx = 0, gy = 0;
         V xr[EPP], xi[EPP], yr[EPP], yi[EPP];
         if (valid) {
-          const R* px = Xr + p * ldp + 2 * gl;
-          const R* pxi = Xi + p * ldp + 2 * gl;
-          const R* py = Xr + q * ldp + 2 * gl;
-          const R* pyi = Xi + q * ldp + 2 * gl;
           V A = splat<V>((R)0), B = A, C = A, D = A;
+          for (int ch = 0; ch < nch; ++ch) {
+            const int c0 = ch * span + 2 * gl;
+            const R* px = Xr + p * ldp + c0;
+            const R* pxi = Xi + p * ldp + c0;
+            const R* py = Xr + q * ldp + c0;
+            const R* pyi = Xi + q * ldp + c0;
 #pragma unroll
-          for (int e = 0; e < EPP; ++e) {
-            xr[e] = *reinterpret_cast<const V*>(px + 2 * gs * e);
-            xi[e] = *reinterpret_cast<const V*>(pxi + 2 * gs * e);
-            yr[e] = *reinterpret_cast<const V*>(py + 2 * gs * e);
-            yi[e] = *reinterpret_cast<const V*>(pyi + 2 * gs * e);
-            // x . conj(y) = (xr yr + xi yi) + i (xi yr - xr yi)
-            A = pfma(xr[e], yr[e], A);
-            B = pfma(xi[e], yi[e], B);
-            C = pfma(xi[e], yr[e], C);
-            D = pfma(xr[e], yi[e], D);
+            for (int e = 0; e < EPP; ++e) {
+              xr[e] = *reinterpret_cast<const V*>(px + 2 * gs * e);
+              xi[e] = *reinterpret_cast<const V*>(pxi + 2 * gs * e);
+              yr[e] = *reinterpret_cast<const V*>(py + 2 * gs * e);
+              yi[e] = *reinterpret_cast<const V*>(pyi + 2 * gs * e);
+              // x . conj(y) = (xr yr + xi yi) + i (xi yr - xr yi)
+              A = pfma(xr[e], yr[e], A);
+              B = pfma(xi[e], yi[e], B);
+              C = pfma(xi[e], yr[e], C);
+              D = pfma(xr[e], yi[e], D);
+            }
           }
           gx = (A.x + A.y) + (B.x + B.y);
           gy = (C.x + C.y) - (D.x + D.y);
@@ -356,17 +362,30 @@ __device__ int jacobi_rows(R* Xr, R* Xi, int ldp, int m, int n, R* nrm, int* nro
           if (rot_params(gx, gy, alpha, beta, tol, cs, sex, sey, tga)) {
             const V CS = splat<V>(cs), SX = splat<V>(sex), SY = splat<V>(sey);
             const V NSX = splat<V>(-sex), NSY = splat<V>(-sey);
-            R* px = Xr + p * ldp + 2 * gl;
-            R* pxi = Xi + p * ldp + 2 * gl;
-            R* py = Xr + q * ldp + 2 * gl;
-            R* pyi = Xi + q * ldp + 2 * gl;
-            // x' = c x - se y ; y' = conj(se) x + c y
+            // one chunk: still in registers; several: each reloaded
+            for (int ch = nch - 1; ch >= 0; --ch) {
+              const int c0 = ch * span + 2 * gl;
+              R* px = Xr + p * ldp + c0;
+              R* pxi = Xi + p * ldp + c0;
+              R* py = Xr + q * ldp + c0;
+              R* pyi = Xi + q * ldp + c0;
+              if (CHUNKED) {
 #pragma unroll
-            for (int e = 0; e < EPP; ++e) {
-              *reinterpret_cast<V*>(px + 2 * gs * e) = pfma(SY, yi[e], pfma(NSX, yr[e], pmul(CS, xr[e])));
-              *reinterpret_cast<V*>(pxi + 2 * gs * e) = pfma(NSY, yr[e], pfma(NSX, yi[e], pmul(CS, xi[e])));
-              *reinterpret_cast<V*>(py + 2 * gs * e) = pfma(SY, xi[e], pfma(SX, xr[e], pmul(CS, yr[e])));
-              *reinterpret_cast<V*>(pyi + 2 * gs * e) = pfma(NSY, xr[e], pfma(SX, xi[e], pmul(CS, yi[e])));
+                for (int e = 0; e < EPP; ++e) {
+                  xr[e] = *reinterpret_cast<const V*>(px + 2 * gs * e);
+                  xi[e] = *reinterpret_cast<const V*>(pxi + 2 * gs * e);
+                  yr[e] = *reinterpret_cast<const V*>(py + 2 * gs * e);
+                  yi[e] = *reinterpret_cast<const V*>(pyi + 2 * gs * e);
+                }
+              }
+              // x' = c x - se y ; y' = conj(se) x + c y
+#pragma unroll
+              for (int e = 0; e < EPP; ++e) {
+                *reinterpret_cast<V*>(px + 2 * gs * e) = pfma(SY, yi[e], pfma(NSX, yr[e], pmul(CS, xr[e])));
+                *reinterpret_cast<V*>(pxi + 2 * gs * e) = pfma(NSY, yr[e], pfma(NSX, yi[e], pmul(CS, xi[e])));
+                *reinterpret_cast<V*>(py + 2 * gs * e) = pfma(SY, xi[e], pfma(SX, xr[e], pmul(CS, yr[e])));
+                *reinterpret_cast<V*>(pyi + 2 * gs * e) = pfma(NSY, xr[e], pfma(SX, xi[e], pmul(CS, yi[e])));
+              }
             }
             if (gl == 0) {
               nrm[p] = alpha - tga;
@@ -983,7 +1002,7 @@ __device__ void qr_precondition_reg(float* Xr, float* Xi, int ldp, int m, int n,
   __shared__ __align__(16) float s_ebr[2][LQBuf<G>::SIZE];
   __shared__ __align__(16) float s_ebi[2][LQBuf<G>::SIZE];
   __shared__ float s_bt2[2];
-  __shared__ float2 s_diag[LT_MAX_DIM];
+  __shared__ float2 s_diag[LT_REG_DIM];
   const int t = threadIdx.x, row = t / G, q = t % G;
   LQRow<G> x;
   __syncthreads();
@@ -1687,8 +1706,8 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
 template <typename R>
 __device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
   blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64 && nJ <= LT_REG_DIM;
-  npad = blocked ? (nJ <= 64 ? 64 : 128)
-                 : 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(nJ);
+  const int span = 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(nJ);
+  npad = blocked ? (nJ <= 64 ? 64 : 128) : span * ((nJ + span - 1) / span);
   mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
 }
 
@@ -1826,7 +1845,12 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
                                    mp2, rr, npad2, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
     } else {
-      sweeps = jacobi_rows<R, BondShape<R>::EPP>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+      if (rr > 2 * BondShape<R>::EPP * 32)
+        sweeps = jacobi_rows<R, BondShape<R>::EPP, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot,
+                                                         a.max_sweeps, a.tol);
+      else
+        sweeps = jacobi_rows<R, BondShape<R>::EPP, false>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot,
+                                                          a.max_sweeps, a.tol);
     }
     // singular values squared, accumulated in double
     {
@@ -3134,7 +3158,8 @@ size_t bond_smem_bytes(int chi, size_t celt, int d) {
     size_t gs = 1;
     while (gs * 2 * epp < n && gs < 32) gs <<= 1;
     const bool blk = single && m >= 32 && n >= 64 && n <= LT_REG_DIM;
-    return blk ? (n <= 64 ? (size_t)64 : (size_t)128) : 2 * epp * gs;
+    const size_t span = 2 * epp * gs;
+    return blk ? (n <= 64 ? (size_t)64 : (size_t)128) : span * ((n + span - 1) / span);
   };
   auto mp_of = [&](size_t m, size_t n) {
     return (single && m >= 32 && n >= 64 && n <= LT_REG_DIM) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
@@ -3443,6 +3468,21 @@ cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev) {
   return cudaGetLastError();
 }
 
+// The dynamic shared-memory ceiling of the bond kernel: 200 KB, or less when the kernel's
+// static shared memory leaves less of the per-block opt-in maximum
+template <typename R, int D>
+static cudaError_t bond_smem_limit(int device, size_t* limit) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, bond_update_kernel<R, D>);
+  if (e != cudaSuccess) return e;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) return e;
+  const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  *limit = room < (size_t)200 * 1024 ? room : (size_t)200 * 1024;
+  return cudaSuccess;
+}
+
 template <typename R, int D>
 static cudaError_t bond_attributes(size_t limit, size_t smem, int* occ) {
   cudaError_t e = cudaFuncSetAttribute(bond_update_kernel<R, D>,
@@ -3455,7 +3495,15 @@ static cudaError_t bond_attributes(size_t limit, size_t smem, int* occ) {
 // attribute setup and occupancy for the bond kernel (called once per context)
 cudaError_t configure_bond(lt_ctx_s* c) {
   const size_t need = bond_smem_bytes(c->chi, c->celt, c->d);
-  const size_t limit = 200 * 1024;
+  size_t limit = 0;
+  cudaError_t el;
+  if (c->d == 4)
+    el = c->prec == LT_MIXED ? bond_smem_limit<float, 4>(c->device, &limit)
+                             : bond_smem_limit<double, 4>(c->device, &limit);
+  else
+    el = c->prec == LT_MIXED ? bond_smem_limit<float, 2>(c->device, &limit)
+                             : bond_smem_limit<double, 2>(c->device, &limit);
+  if (el != cudaSuccess) return el;
   c->bond_use_smem = need <= limit;
   c->bond_smem = c->bond_use_smem ? need : 0;
   cudaError_t e;

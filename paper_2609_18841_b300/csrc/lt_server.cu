@@ -36,6 +36,7 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
   std::vector<double> mean, sem;
   lt_status status = LT_OK;
+  uint64_t updates = 0;  // two-site updates the request executed (its context's counter)
   std::string error;  // the context's last error when the request failed
   int state = 0;      // 0 queued, 1 active, 2 finished (status tells success)
 };
@@ -89,6 +90,9 @@ void retire(lt_server_s* s, Request& r, lt_status st) {
     if (st != LT_OK) {
       const char* e = lt_last_error(r.ctx);
       r.error = e ? e : "";
+    } else {
+      uint64_t cnt[LT_NCOUNTERS] = {0};
+      if (lt_get_counters(r.ctx, cnt, 0) == LT_OK) r.updates = cnt[0];
     }
     s->used -= r.bytes;
     lt_destroy(r.ctx);
@@ -279,6 +283,15 @@ lt_status lt_server_result(lt_server s, int64_t id, double* mean, double* sem, d
   if (r.status != LT_OK) return r.status;
   if (mean) std::memcpy(mean, r.mean.data(), sizeof(double) * r.cfg.L);
   if (sem) std::memcpy(sem, r.sem.data(), sizeof(double) * r.cfg.L);
+  return LT_OK;
+}
+
+lt_status lt_server_updates(lt_server s, int64_t id, uint64_t* updates) {
+  if (!s || !updates) return LT_ERR_ARG;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return LT_ERR_ARG;
+  if (it->second.state != 2) return LT_ERR_STATE;
+  *updates = it->second.updates;
   return LT_OK;
 }
 

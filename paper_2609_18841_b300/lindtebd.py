@@ -42,7 +42,7 @@ EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_ap
            "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step", "lt_pipe_peaks",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
            "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
-           "lt_server_result", "lt_server_error", "lt_server_usage"]
+           "lt_server_result", "lt_server_error", "lt_server_usage", "lt_server_updates"]
 
 
 def load_library(path=LIB_PATH):
@@ -84,6 +84,7 @@ def load_library(path=LIB_PATH):
         "lt_server_tick": ([P, P, P, P], I32),
         "lt_server_result": ([P, I64, P, P, P], I32),
         "lt_server_usage": ([P, P, P], I32),
+        "lt_server_updates": ([P, I64, P], I32),
         "lt_server_error": ([P, I64], ctypes.c_char_p),
         "lt_last_error": ([P], ctypes.c_char_p),
     }
@@ -439,6 +440,12 @@ class Server:
 
     def error(self, rid):
         return _lib.lt_server_error(self.h, rid).decode()
+
+    def updates(self, rid):
+        """Two-site updates a finished request executed."""
+        u = np.zeros(1, np.uint64)
+        _check(_lib.lt_server_updates(self.h, rid, _ptr(u)), "lt_server_updates")
+        return int(u[0])
 
     def usage(self):
         u = np.zeros(2, np.uint64)

@@ -35,15 +35,15 @@ def test_config_struct_layout_matches_header():
 
 
 @pytest.mark.parametrize("kw,status", [
-    (dict(L=1), 1), (dict(chi_max=0), 1), (dict(chi_max=129), 1), (dict(n_traj=0), 1),
+    (dict(L=1), 1), (dict(chi_max=0), 1), (dict(chi_max=257), 1), (dict(n_traj=0), 1),
     (dict(dt=0.0), 1), (dict(trotter_order=3), 1), (dict(precision=5), 1),
     (dict(method=1, gamma_loss=0.1), 7), (dict(method=4), 7), (dict(gamma_loss=-0.1), 1),
-    # the purified density matrix: Kraus dimension 2 only, chi_max <= 64, local jumps
-    (dict(method=3, kraus_dim=3), 7), (dict(method=3, chi_max=65), 7),
+    # the purified density matrix: Kraus dimension 2 only, chi_max <= 128, local jumps
+    (dict(method=3, kraus_dim=3), 7), (dict(method=3, chi_max=129), 7),
     (dict(method=3, gamma_gain=[0, 0.1, 0, 0, 0, 0, 0, 0]), 7),
-    # the vectorised density matrix: theta is 4 chi wide (chi_max <= 64), and a
+    # the vectorised density matrix: theta is 4 chi wide (chi_max <= 128), and a
     # fermionic loss or gain is local only on the chain ends
-    (dict(method=2, chi_max=65), 7), (dict(method=2, chi_max=129), 1),
+    (dict(method=2, chi_max=129), 7), (dict(method=2, chi_max=257), 1),
     (dict(method=2, gamma_loss=[0, 0, 0.1, 0, 0, 0, 0, 0]), 7),
     (dict(method=2, gamma_gain=[0, 0, 0, 0, 0, 0, 0.2, 0]), 7),
     (dict(init="product"), 1),

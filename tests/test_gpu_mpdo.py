@@ -260,3 +260,34 @@ def test_mpdo_edges(name, cfg, steps):
     close(per[0], res["density"], FP64_TOL, "density")
     close(Cp[0], res["corr"], FP64_TOL, "corr")
     assert list(dims[0]) == list(res["bond_dims"])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_configured_chi128_theta_512(precision, tol):
+    # chi_max = 128, the vectorised density matrix's configured bond dimension: bond 4
+    # of a 10-site chain with dims 128 | 128 | 128 has theta 512 x 512 (rows longer than
+    # one Jacobi group's span, handled in chunks); bond 2 is 64 x 512.  Synthetic state.
+    from paper_2609_18841_b300.lindtebd import unpack_state
+    lt = _lt()
+    L, chi = 10, 128
+    dims = [4, 16, 64, 128, 128, 128, 64, 16, 4]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=16, d=4, dims=dims)
+    cut = 1e-12 if precision == "fp64" else 1e-6
+    cfg = cfg_of(L, chi, loss=0.1, gain=0.05, cut=cut)
+    ref = mpdo.MPDO(cfg)
+    ref.B, ref.lam = [b.copy() for b in B], [x.copy() for x in lam]
+    ref.apply_layer(0, mpdo.bond_gates(cfg, 0.02))
+    prec = lt.LT_FP64 if precision == "fp64" else lt.LT_MIXED
+    with ensemble(cfg, 1, prec) as e:
+        e.set_state(0, [(B, lam, dims)])
+        e.apply_layer(0, 0.02)
+        gd, gl, gB = e.get_state(0, 1)
+    gBs, gls = unpack_state(gd[0], gl[0], gB[0], L, d=4)
+    for b in (0, 2, 4, 6, 8):
+        X = np.tensordot(ref.B[b], ref.B[b + 1], axes=(2, 0)).reshape(4 * ref.B[b].shape[0], -1)
+        Y = np.tensordot(gBs[b], gBs[b + 1], axes=(2, 0)).reshape(4 * gBs[b].shape[0], -1)
+        w = np.repeat(ref.lam[b - 1], 4)[:, None] if b > 0 else np.ones((4, 1))
+        err = np.abs(w * (Y - X)).max() / np.abs(w * X).max()
+        assert err < tol, "bond %d: relative error %.2e" % (b, err)
+    if precision == "fp64":
+        assert list(gd[0]) == ref.bond_dims()

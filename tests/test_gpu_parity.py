@@ -448,3 +448,34 @@ def test_w1_sampled_decisions_agree_between_precisions():
     print("W1 sampled decisions: %d of %d trajectories part, %d of %d trajectory-steps differ"
           % (len(parted), n, int((a != b).sum()), a.size))
     assert len(parted) <= 0.02 * n
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_chi256_theta_512(precision, tol):
+    # chi_max = 256 (the serving mix's largest): bond 8 of an 18-site chain with dims
+    # 256 | 256 | 256 has theta 512 x 512; one layer against the oracle's update of the
+    # same synthetic state (the gauge-invariant two-site blocks, as above)
+    from paper_2609_18841_b300.lindtebd import unpack_state
+    lt = _lt()
+    L, chi = 18, 256
+    dims = [min(2 ** (b + 1), 2 ** (L - b - 1), chi) for b in range(L - 1)]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=18, dims=dims)
+    cut = 1e-12 if precision == "fp64" else 1e-6
+    cfg = tebd.TrajectoryConfig(L, J=1.0, dt=0.02, chi_max=chi, svd_cut=cut, gamma_loss=0.2,
+                                occupation=workloads.occupation(L, "neel"))
+    ref = tebd.Trajectory.from_tensors(cfg, B, lam)
+    ref.apply_layer(0, cfg.gates(0.02))
+    prec = lt.LT_FP64 if precision == "fp64" else lt.LT_MIXED
+    with lt.Ensemble(L, chi, 1, precision=prec, dt=0.02, gamma_loss=0.2, svd_cut=cut) as e:
+        e.set_state(0, [(B, lam, dims)])
+        e.apply_layer(0, 0.02)
+        gd, gl, gB = e.get_state(0, 1)
+    gBs, gls = unpack_state(gd[0], gl[0], gB[0], L)
+    bonds = list(range(0, L - 1, 2))
+    want = _two_site_blocks(ref.B, ref.lam, bonds, 2)
+    got = _two_site_blocks(gBs, gls, bonds, 2)
+    for b in bonds:
+        err = np.abs(got[b] - want[b]).max() / np.abs(want[b]).max()
+        assert err < tol, "bond %d: relative error %.2e" % (b, err)
+    if precision == "fp64":
+        assert list(gd[0]) == ref.bond_dims()

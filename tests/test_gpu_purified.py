@@ -154,3 +154,34 @@ def test_purified_edges(name, cfg, steps):
     close(per[0], res["density"], FP64_TOL, "density")
     close(Cp[0], res["corr"], FP64_TOL, "corr")
     assert list(dims[0]) == list(res["bond_dims"])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_configured_chi96_theta_384(precision, tol):
+    # chi_max = 96, the purified form's configured bond dimension: bond 4 of a 10-site
+    # chain with dims 96 | 96 | 96 has theta 384 x 384 (s = 2n + k, four values per
+    # site); the layer keeps the norm change.  Synthetic state.
+    from paper_2609_18841_b300.lindtebd import unpack_state
+    lt = _lt()
+    L, chi = 10, 96
+    dims = [4, 16, 64, 96, 96, 96, 64, 16, 4]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=17, d=4, dims=dims)
+    cut = 1e-12 if precision == "fp64" else 1e-6
+    cfg = cfg_of(L, chi, loss=0.1, deph=0.05, cut=cut)
+    ref = purified.Purified(cfg, 2)
+    ref.B, ref.lam = [b.copy() for b in B], [x.copy() for x in lam]
+    ref.apply_layer(0, [purified.full_gate(G, 2) for G in cfg.gates(0.01)])
+    prec = lt.LT_FP64 if precision == "fp64" else lt.LT_MIXED
+    with ensemble(cfg, 1, prec) as e:
+        e.set_state(0, [(B, lam, dims)])
+        e.apply_layer(0, 0.01)
+        gd, gl, gB = e.get_state(0, 1)
+    gBs, gls = unpack_state(gd[0], gl[0], gB[0], L, d=4)
+    for b in (0, 2, 4, 6, 8):
+        X = np.tensordot(ref.B[b], ref.B[b + 1], axes=(2, 0)).reshape(4 * ref.B[b].shape[0], -1)
+        Y = np.tensordot(gBs[b], gBs[b + 1], axes=(2, 0)).reshape(4 * gBs[b].shape[0], -1)
+        w = np.repeat(ref.lam[b - 1], 4)[:, None] if b > 0 else np.ones((4, 1))
+        err = np.abs(w * (Y - X)).max() / np.abs(w * X).max()
+        assert err < tol, "bond %d: relative error %.2e" % (b, err)
+    if precision == "fp64":
+        assert list(gd[0]) == ref.bond_dims()

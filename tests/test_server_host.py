@@ -17,7 +17,7 @@ def test_context_bytes_scales_with_the_ensemble():
     assert lt.lt_context_bytes(32, 64, 16, **base) < b1
     assert lt.lt_context_bytes(64, 32, 16, **base) < b1
     with pytest.raises(lt.LtError):
-        lt.lt_context_bytes(64, 129, 16, **base)
+        lt.lt_context_bytes(64, 257, 16, **base)
 
 
 def test_context_bytes_of_a_vectorised_density_matrix():

@@ -56,7 +56,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     p = d.data_ptr()
     # (L + 8) chi^2 complex128 per trajectory: L = 600, chi = 64 needs 38 MiB > 32 MiB
     assert lt.lt_measure_density_noalloc(lt.LT_FP64, 600, 64, 1, p, p, p, None) == lt.LT_ERR_ARG
-    assert lt.lt_measure_density_noalloc(lt.LT_FP64, 8, 129, 1, p, p, p, None) == lt.LT_ERR_ARG
+    assert lt.lt_measure_density_noalloc(lt.LT_FP64, 8, 257, 1, p, p, p, None) == lt.LT_ERR_ARG
     assert lt.lt_measure_density_noalloc(lt.LT_MIXED, 8, 8, 1, p, None, p, None) == lt.LT_ERR_ARG
     assert lt.lt_measure_density_noalloc(lt.LT_FP64, 8, 8, 0, p, p, p, None) == lt.LT_ERR_ARG
 
