@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--qsd-traj", type=int, default=1024)
     ap.add_argument("--qsd-steps", type=int, default=2)
     ap.add_argument("--qsd-chi128-traj", type=int, default=64)
+    ap.add_argument("--qsd-full-traj", type=int, default=1024)
+    ap.add_argument("--qsd-cap-s", type=float, default=30.0)
     ap.add_argument("--mpdo-steps", type=int, default=250)
     ap.add_argument("--mpdo-sat-steps", type=int, default=2)
     ap.add_argument("--dm-cap-s", type=float, default=45.0)
@@ -57,7 +59,7 @@ def parse():
     ap.add_argument("--purified-steps", type=int, default=50)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-cap-s", type=float, default=90.0)
+    ap.add_argument("--serve-cap-s", type=float, default=60.0)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--acc-steps", type=int, default=2)
     ap.add_argument("--full-traj", type=int, default=512)
@@ -462,7 +464,7 @@ def serving_leg(lt, args):
             if method == lt.LT_PURIFIED:
                 kw["kraus_dim"] = 2
         reqs.append(kw)
-    failed, lat, upd, done_ids = {}, [], 0, set()
+    failed, lat, upd, upd_all, done_ids = {}, [], 0, 0, set()
     with lt.Server(args.serve_budget_gb << 30, 64) as srv:
         ids, k = [], 0
         t0 = time.perf_counter()
@@ -480,6 +482,7 @@ def serving_leg(lt, args):
                 time.sleep(max(0.0, min(0.002, arrivals[k] - now)))
         wall = time.perf_counter() - t0
         for rid in ids:
+            upd_all += srv.updates(rid)   # finished, or done so far by an active request
             try:
                 st, _, _, t = srv.result(rid)
             except Exception:
@@ -497,6 +500,7 @@ def serving_leg(lt, args):
             "unfinished_at_cap": unfinished, "cap_s": cap, "arrival_rate_per_s": rate,
             "wall_s": wall, "completed_per_s": len(lat) / wall,
             "updates_per_s_completed": upd / wall,
+            "updates_per_s_all": upd_all / wall,
             "latency_s": {"p50": float(np.percentile(lat, 50)),
                           "p99": float(np.percentile(lat, 99))} if lat else None,
             "mix": "Poisson arrivals at %g/s; method trajectory, QSD, MPDO or purified "
@@ -670,15 +674,36 @@ def run_ours(args):
     del ens
     torch.cuda.synchronize()
 
+    # secondary legs: an ensemble a leg opens is closed whatever happens in it, and
+    # after a CUDA error (the context is then unusable) the remaining legs are skipped
+    opened = []
+    dead = []
+
+    def reg(e):
+        opened.append(e)
+        return e
+
+    def close_open():
+        while opened:
+            try:
+                opened.pop().close()
+            except Exception:
+                pass
+
+    def failed(err):
+        if isinstance(err, lt.LtError) and err.status == lt.LT_ERR_CUDA:
+            dead.append(repr(err))
+        return {"error": repr(err)}
+
     # ---- plain FP64 path on a subset (same kernels in double precision) ----------------
     fp64 = None
     try:
         # single-GPU legs run at N = 1 only (in a scaling run they would hold every GPU)
         solo = world == 1
-        if args.fp64_traj > 0 and solo:
+        if args.fp64_traj > 0 and solo and not dead:
             n64 = args.fp64_traj
-            e64 = lt.Ensemble(L, chi, n64, precision=lt.LT_FP64, init="neel",
-                              stream=stream.cuda_stream, **w3_kwargs("fp64"))
+            e64 = reg(lt.Ensemble(L, chi, n64, precision=lt.LT_FP64, init="neel",
+                              stream=stream.cuda_stream, **w3_kwargs("fp64")))
             upload(lt, e64.ctx, packed, n64)
             lt.lt_step(e64.ctx, 1)
             torch.cuda.synchronize()
@@ -701,17 +726,19 @@ def run_ours(args):
                                          "over its wall time"}}
             e64.close()
     except Exception as err:  # recorded in the line; the headline still prints
-        fp64 = {"error": repr(err)}
+        fp64 = failed(err)
+    finally:
+        close_open()
 
     # ---- quantum state diffusion leg (Sec. 5.2), one GPU -------------------------------
     qsd = None
     try:
-        if args.qsd_traj > 0 and solo:
+        if args.qsd_traj > 0 and solo and not dead:
             Lq, nq, dtq = 128, args.qsd_traj, 0.01
             mq, pq = state_pool(Lq, chi, POOL, seed=4321)
-            eq = lt.Ensemble(Lq, chi, nq, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
+            eq = reg(lt.Ensemble(Lq, chi, nq, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
                              dt=dtq, gamma_loss=0.05, gamma_deph=0.1, fermionic_jumps=0,
-                             svd_cut=1e-6, stream=stream.cuda_stream)
+                             svd_cut=1e-6, stream=stream.cuda_stream))
             upload(lt, eq.ctx, pq, nq)
             lt.lt_step(eq.ctx, 1)
             torch.cuda.synchronize()
@@ -741,9 +768,9 @@ def run_ours(args):
             if args.qsd_chi128_traj > 0:
                 n8 = args.qsd_chi128_traj
                 m8, p8 = state_pool(Lq, 128, 8, seed=4321)
-                e8 = lt.Ensemble(Lq, 128, n8, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
+                e8 = reg(lt.Ensemble(Lq, 128, n8, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
                                  dt=dtq, gamma_loss=0.05, gamma_deph=0.1, fermionic_jumps=0,
-                                 svd_cut=1e-6, stream=stream.cuda_stream)
+                                 svd_cut=1e-6, stream=stream.cuda_stream))
                 upload(lt, e8.ctx, p8, n8)
                 torch.cuda.synchronize()
                 e8.counters(clear=True)
@@ -758,20 +785,54 @@ def run_ours(args):
                                  "layer_updates_per_s": c8["layer_updates"] / s8}
                 e8.close()
                 del m8, p8
+            # the QSD configuration as written: L=128, chi_max=128, 1024 histories from
+            # the Neel state to T=2 (200 steps of 0.01), stopped at args.qsd_cap_s
+            if args.qsd_full_traj > 0:
+                nf = args.qsd_full_traj
+                ef = reg(lt.Ensemble(Lq, 128, nf, method=lt.LT_QSD, precision=lt.LT_MIXED,
+                                     init="neel", dt=dtq, gamma_loss=0.05, gamma_deph=0.1,
+                                     fermionic_jumps=0, svd_cut=1e-6, stream=stream.cuda_stream))
+                torch.cuda.synchronize()
+                ef.counters(clear=True)
+                sf, doneq = 0.0, 0
+                while doneq < 200 and sf < args.qsd_cap_s:
+                    a.record(stream)
+                    lt.lt_step(ef.ctx, 10)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    sf += a.elapsed_time(b) / 1e3
+                    doneq += 10
+                cf = ef.counters()
+                _, dimsf = ef.stats()
+                lwf = ef.log_weights()
+                qsd["config_T2"] = {
+                    "workload": "QSD as configured: L=128, chi_max=128, %d histories from the Neel "
+                                "state, dephasing 0.1 and spin loss 0.05, dt=0.01, T=2 (200 steps), "
+                                "mixed precision" % nf,
+                    "steps_done": doneq, "T_reached": doneq * dtq, "stopped_at_cap": doneq < 200,
+                    "cap_s": args.qsd_cap_s, "s": sf, "ms_per_step": 1e3 * sf / doneq,
+                    "updates_per_s": cf["updates"] / sf,
+                    "history_steps_per_s": nf * doneq / sf,
+                    "final_max_bond_dim": int(dimsf.max()),
+                    "final_mean_bond_dim": float(dimsf.mean()),
+                    "log_weight_range": [float(lwf.min()), float(lwf.max())]}
+                ef.close()
     except Exception as err:  # recorded in the line; the headline still prints
-        qsd = {"error": repr(err)}
+        qsd = failed(err)
+    finally:
+        close_open()
 
     # ---- density-matrix legs: vectorised (Sec. 3.1) and purified (Sec. 3.2), one GPU ---
     mpdo_leg = purified_leg = None
     try:
-        if args.mpdo_steps > 0 and solo:
+        if args.mpdo_steps > 0 and solo and not dead:
             mpdo_leg = density_matrix_leg(
                 lt, stream, args, alu_peak, method=lt.LT_MPDO, L=32, chi=128, init="domain_wall",
                 rates=dict(dt=0.02, gamma_loss=0.1, gamma_gain=0.05), steps=args.mpdo_steps,
                 workload="MPDO (d^2 = 4): L=32 XX chain, spin loss 0.1 and gain 0.05 on every site, "
                          "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=128 (theta up to "
                          "512 x 512)")
-        if args.purified_steps > 0 and solo:
+        if args.purified_steps > 0 and solo and not dead:
             purified_leg = density_matrix_leg(
                 lt, stream, args, alu_peak, method=lt.LT_PURIFIED, L=64, chi=96, init="neel",
                 rates=dict(dt=0.01, gamma_loss=0.05, gamma_deph=0.1), steps=args.purified_steps,
@@ -779,26 +840,25 @@ def run_ours(args):
                          "dephasing 0.1 and spin loss 0.05 on every site, dt=0.01, 2nd-order Trotter "
                          "then the R step, Neel start, chi_max=96 (theta up to 384 x 384)")
     except Exception as err:  # recorded in the line; the headline still prints
-        mpdo_leg = {"error": repr(err)}
-        purified_leg = {"error": repr(err)}
+        mpdo_leg = purified_leg = failed(err)
 
     # ---- serving: the configured request mix (Poisson arrivals) through the server ------
     serving = None
     try:
-        if args.serve_requests > 0 and solo:
+        if args.serve_requests > 0 and solo and not dead:
             serving = serving_leg(lt, args)
     except Exception as err:  # recorded in the line; the headline still prints
-        serving = {"error": repr(err)}
+        serving = failed(err)
 
     # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
     accuracy = None
     try:
-        if args.acc_traj > 0 and solo:
+        if args.acc_traj > 0 and solo and not dead:
             na = args.acc_traj
-            ea = lt.Ensemble(L, chi, na, precision=lt.LT_FP64, init="neel",
-                             stream=stream.cuda_stream, **w3_kwargs("fp64"))
-            em = lt.Ensemble(L, chi, na, precision=lt.LT_MIXED, init="neel",
-                             stream=stream.cuda_stream, **w3_kwargs("mixed"))
+            ea = reg(lt.Ensemble(L, chi, na, precision=lt.LT_FP64, init="neel",
+                             stream=stream.cuda_stream, **w3_kwargs("fp64")))
+            em = reg(lt.Ensemble(L, chi, na, precision=lt.LT_MIXED, init="neel",
+                             stream=stream.cuda_stream, **w3_kwargs("mixed")))
             upload(lt, ea.ctx, packed, na)
             upload(lt, em.ctx, packed, na)
             jumps = 0
@@ -823,20 +883,22 @@ def run_ours(args):
             ea.close()
             em.close()
     except Exception as err:  # recorded in the line; the headline still prints
-        accuracy = {"error": repr(err)}
+        accuracy = failed(err)
+    finally:
+        close_open()
 
     # ---- the configured W3 run to T = 4 from the Neel state --------------------------------
     full = None
     try:
-        if args.full_traj > 0 and solo:
+        if args.full_traj > 0 and solo and not dead:
             full = w3_full_run_leg(lt, stream, args)
     except Exception as err:  # recorded in the line; the headline still prints
-        full = {"error": repr(err)}
+        full = failed(err)
 
     # ---- end to end through the public API with host buffers ---------------------------
     e2e = None
     try:
-        if not args.no_e2e:
+        if not args.no_e2e and not dead:
             dims, lam, B = packed
             pinned = [torch.from_numpy(x).pin_memory().numpy() for x in (dims, lam, B)]
             mean_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
@@ -873,7 +935,7 @@ def run_ours(args):
                                "memory, %d x (lt_step + lt_measure_density to host), lt_destroy"
                                % args.steps}
     except Exception as err:  # recorded in the line; the headline still prints
-        e2e = {"error": repr(err)}
+        e2e = failed(err)
 
     cpu = None
     if solo and not args.no_cpu:

@@ -93,11 +93,23 @@ typedef struct {
   int64_t traj_offset;       /* global id of trajectory 0 (Philox counter word 0)  */
   double jacobi_tol;         /* rotate a row pair while |x.y^+| > tol |x| |y|;     */
                              /* 0 = default eps sqrt(n) of the working precision   */
-  int32_t theta_simt;        /* LT_MIXED with two values per site: 0 (default)     */
-                             /* forms theta on the tensor cores from exact 8-bit   */
-                             /* digit products (error below the final rounding);   */
-                             /* 1 forms it with single-precision FMAs              */
+  int32_t theta_path;        /* LT_MIXED, two values per site: 0 = the tuned        */
+                             /* schedule's choice, 1 = tensor cores (exact 8-bit   */
+                             /* digit products, error below the final rounding),   */
+                             /* 2 = single-precision FMAs                          */
+  int32_t jacobi_epp;        /* element pairs per lane of the row-pair Jacobi that  */
+                             /* takes theta wider than 128: 0 = tuned, 4, or 8     */
+                             /* (8 in LT_MIXED only)                               */
+  int32_t env_ctas_per_sm;   /* CTAs per SM of the environment kernels (rates and  */
+                             /* observables): 0 = tuned, 1..8                      */
 } lt_config;
+
+/* Schedules.  The fields theta_path, jacobi_epp and env_ctas_per_sm left at 0 take
+ * the values of a table the library carries, written by the autotuner
+ * (paper_2609_18841_b300/autotune.py) from timings on the device: for each number of
+ * values per site (2 or 4), precision and chi_max (the smallest tabulated chi_max at
+ * or above the context's), the candidate schedule with the shortest time step.
+ * Without an entry: tensor cores, 4 element pairs, up to 8 CTAs per SM. */
 
 /* Create a context: validate cfg, allocate the ensemble on the current device
  * and set every trajectory to the initial product state (Sec. 4.1: the
@@ -317,9 +329,9 @@ lt_status lt_server_tick(lt_server server, int32_t* n_queued, int32_t* n_active,
  * it failed (times are still written). */
 lt_status lt_server_result(lt_server server, int64_t id, double* mean, double* sem,
                            double* times);
-/* Two-site updates a finished request executed (its context's work counter,
- * lt_get_counters out[0], read at retirement; 0 if it failed).  LT_ERR_STATE while
- * it runs. */
+/* Two-site updates a request executed (its context's work counter, lt_get_counters
+ * out[0]): for a finished request as read at retirement (0 if it failed), for an
+ * active one so far (this synchronises its stream), 0 while it is queued. */
 lt_status lt_server_updates(lt_server server, int64_t id, uint64_t* updates);
 /* Why a finished request failed (the failing call and the CUDA message), "" if
  * it succeeded or is unknown; valid until the server is destroyed. */

@@ -595,11 +595,11 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
   return sweep + 1;
 }
 
-// launch shape per precision: 256 threads; the pair Jacobi holds 8 (single) or
-// 4 (double) element pairs of each row per lane
+// threads per CTA of the bond kernel per precision (the row-pair Jacobi holds 4 element
+// pairs of each row per lane, or 8 in single precision when the schedule says so)
 template <typename R> struct BondShape;
-template <> struct BondShape<float> { static constexpr int NT = 512, EPP = 4; };
-template <> struct BondShape<double> { static constexpr int NT = 256, EPP = 4; };
+template <> struct BondShape<float> { static constexpr int NT = 512; };
+template <> struct BondShape<double> { static constexpr int NT = 256; };
 
 // ---- two-level Householder preconditioning of the row Jacobi ---------------------------
 // The one-sided Jacobi on the rows of X converges slowly when the rows are
@@ -1240,7 +1240,7 @@ __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, i
 // scratch array Es (k x k complex); the product runs in column chunks held in registers.
 template <int NT>
 __device__ void reorthonormalise_rows(float2* Y, int ld, int k, int n, float2* Es) {
-  constexpr int NW = NT / 32, PER = 16;
+  constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = warp; j < k; j += NW) {
     double acc = 0.0;
@@ -1259,41 +1259,81 @@ __device__ void reorthonormalise_rows(float2* Y, int ld, int k, int n, float2* E
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < k * k; idx += NT) {
-    const int i = idx / k, j = idx - i * k;
-    float2 acc = make_float2(0.f, 0.f);
-    if (i != j) {
-      const float2* yi = Y + i * ld;
-      const float2* yj = Y + j * ld;
-      for (int c = 0; c < n; ++c) cfmac(acc, yi[c], yj[c]);  // sum_c y_i conj(y_j)
+  // E[i][j] = sum_c y_i conj(y_j) (i != j, E[j][i] its conjugate, zero diagonal): 2 x 2
+  // tiles of the upper triangle, four complex products per four loads
+  const int kb = (k + 1) >> 1, ntile = kb * (kb + 1) / 2;
+  for (int t = tid; t < ntile; t += NT) {
+    int I = 0, rem = t;
+    while (rem >= kb - I) {  // row I of the triangle holds kb - I tiles
+      rem -= kb - I;
+      ++I;
     }
-    Es[idx] = acc;
+    const int J = I + rem;
+    const int i0 = 2 * I, i1 = i0 + 1, j0 = 2 * J, j1 = j0 + 1;
+    const bool vi1 = i1 < k, vj1 = j1 < k;
+    const float2* y0 = Y + i0 * ld;
+    const float2* y1 = Y + (vi1 ? i1 : i0) * ld;
+    const float2* z0 = Y + j0 * ld;
+    const float2* z1 = Y + (vj1 ? j1 : j0) * ld;
+    float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
+    for (int c = 0; c < n; ++c) {
+      const float2 u0 = y0[c], u1 = y1[c], v0 = z0[c], v1 = z1[c];
+      cfmac(a00, u0, v0);
+      cfmac(a01, u0, v1);
+      cfmac(a10, u1, v0);
+      cfmac(a11, u1, v1);
+    }
+    const float2 zero = make_float2(0.f, 0.f);
+    auto put = [&](int i, int j, float2 v) {
+      Es[i * k + j] = i == j ? zero : v;
+      if (i != j) Es[j * k + i] = make_float2(v.x, -v.y);
+    };
+    put(i0, j0, a00);
+    if (vj1) put(i0, j1, a01);
+    if (vi1 && I != J) put(i1, j0, a10);
+    if (vi1 && vj1) put(i1, j1, a11);
   }
   __syncthreads();
-  const int cw = (NT * PER) / k < n ? ((NT * PER) / k > 0 ? (NT * PER) / k : 1) : n;
+  // Y <- Y - E Y / 2: an item is four rows of one column; each load of Y[j][c] feeds the
+  // four rows, E is read as a broadcast within the warp
+  constexpr int RG = 4, ITEMS = 4;
+  const int kg = (k + RG - 1) / RG;
+  const int cw = (NT * ITEMS) / kg < n ? ((NT * ITEMS) / kg > 0 ? (NT * ITEMS) / kg : 1) : n;
   for (int c0 = 0; c0 < n; c0 += cw) {
     const int w = n - c0 < cw ? n - c0 : cw;
-    float2 acc[PER];
+    float2 acc[ITEMS][RG];
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      acc[p] = make_float2(0.f, 0.f);
-      const int idx = tid + NT * p;
-      if (idx < k * w) {
-        const int i = idx / w, c = c0 + idx - i * w;
-        const float2* e = Es + i * k;
-        for (int j = 0; j < k; ++j) cfma(acc[p], e[j], Y[j * ld + c]);
+    for (int it = 0; it < ITEMS; ++it) {
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[it][r] = make_float2(0.f, 0.f);
+      const int item = tid + NT * it;
+      if (item < kg * w) {
+        const int g = item / w, c = c0 + item - g * w;
+        const float2* e0 = Es + (RG * g) * k;
+        for (int j = 0; j < k; ++j) {
+          const float2 y = Y[j * ld + c];
+#pragma unroll
+          for (int r = 0; r < RG; ++r)
+            if (RG * g + r < k) cfma(acc[it][r], e0[r * k + j], y);
+        }
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int idx = tid + NT * p;
-      if (idx < k * w) {
-        const int i = idx / w, c = c0 + idx - i * w;
-        float2 v = Y[i * ld + c];
-        v.x = fmaf(-0.5f, acc[p].x, v.x);
-        v.y = fmaf(-0.5f, acc[p].y, v.y);
-        Y[i * ld + c] = v;
+    for (int it = 0; it < ITEMS; ++it) {
+      const int item = tid + NT * it;
+      if (item < kg * w) {
+        const int g = item / w, c = c0 + item - g * w;
+#pragma unroll
+        for (int r = 0; r < RG; ++r) {
+          const int i = RG * g + r;
+          if (i < k) {
+            float2 v = Y[i * ld + c];
+            v.x = fmaf(-0.5f, acc[it][r].x, v.x);
+            v.y = fmaf(-0.5f, acc[it][r].y, v.y);
+            Y[i * ld + c] = v;
+          }
+        }
       }
     }
     __syncthreads();
@@ -1704,9 +1744,10 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
 }
 
 template <typename R>
-__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
+__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp,
+                                              int epp) {
   blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64 && nJ <= LT_REG_DIM;
-  const int span = 2 * BondShape<R>::EPP * jacobi_span<R, BondShape<R>::EPP>(nJ);
+  const int span = epp == 8 ? 16 * jacobi_span<R, 8>(nJ) : 8 * jacobi_span<R, 4>(nJ);
   npad = blocked ? (nJ <= 64 ? 64 : 128) : span * ((nJ + span - 1) / span);
   mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
 }
@@ -1748,7 +1789,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     const int nJ = mode == 2 ? chiM : D * chiR;
     bool blocked;
     int npad, mpJ;
-    jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ);
+    jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ, a.epp);
     // two-level Householder preconditioning; the Jacobi then acts on the r x r
     // upper-triangular factor, whose window (mp2 x npad2) can have more rows than
     // the mJ x nJ layout: a wide matrix (nJ > LT_REG_DIM, rows rounded to even)
@@ -1758,7 +1799,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     const int rr = mJ < nJ ? mJ : nJ;
     bool blk2;
     int npad2, mp2;
-    jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
+    jacobi_layout<R>(rr, rr, blk2, npad2, mp2, a.epp);
     const int mpad = mpJ > mp2 ? mpJ : mp2;
     const int mcap = mode == 1 ? (mpad > D * chiL ? mpad : D * chiL) : mpad;
     const int ldp = npad + 2, ld = nJ + 1;
@@ -1845,12 +1886,18 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
                                    mp2, rr, npad2, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
     } else {
-      if (rr > 2 * BondShape<R>::EPP * 32)
-        sweeps = jacobi_rows<R, BondShape<R>::EPP, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot,
-                                                         a.max_sweeps, a.tol);
-      else
-        sweeps = jacobi_rows<R, BondShape<R>::EPP, false>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot,
-                                                          a.max_sweeps, a.tol);
+      // element pairs per lane of the row-pair Jacobi: 4, or 8 in single precision when
+      // the schedule says so (one group then spans twice the columns)
+      if (sizeof(R) == 4 && a.epp == 8) {
+        if (rr > 2 * 8 * 32)
+          sweeps = jacobi_rows<R, 8, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+        else
+          sweeps = jacobi_rows<R, 8, false>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+      } else if (rr > 2 * 4 * 32) {
+        sweeps = jacobi_rows<R, 4, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+      } else {
+        sweeps = jacobi_rows<R, 4, false>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
+      }
     }
     // singular values squared, accumulated in double
     {
@@ -3146,14 +3193,14 @@ inline int grid_for(long long n, int block) {
 }  // namespace
 
 // ---- launchers -------------------------------------------------------------------------------
-size_t bond_smem_bytes(int chi, size_t celt, int d) {
+size_t bond_smem_bytes(int chi, size_t celt, int d, int epp) {
   // Largest workspace of a task, in complex elements, over the three modes with
   // every dimension at chi and d physical values per site (mirrors the layout of
   // bond_update_kernel): the Jacobi matrix planar mcap x (npad + 2), V_k^+
   // k x (nJ + 1), plus the staging of B_{b+1} (mode 0) or of the new site
   // tensors (mode 2).
   const bool single = celt == sizeof(float2);
-  const size_t epp = single ? BondShape<float>::EPP : BondShape<double>::EPP;
+  if (!single || epp != 8) epp = 4;
   auto npad_of = [&](size_t m, size_t n) {
     size_t gs = 1;
     while (gs * 2 * epp < n && gs < 32) gs <<= 1;
@@ -3215,7 +3262,8 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.nb = nb;
   a.gates = gates;
   a.mode = mode;
-  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt, D) / c->celt);
+  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt, D, c->epp) / c->celt);
+  a.epp = sizeof(R) == 4 && c->epp == 8 ? 8 : 4;
   a.L = c->L;
   a.chi = c->chi;
   a.slot = c->slot;
@@ -3494,7 +3542,7 @@ static cudaError_t bond_attributes(size_t limit, size_t smem, int* occ) {
 
 // attribute setup and occupancy for the bond kernel (called once per context)
 cudaError_t configure_bond(lt_ctx_s* c) {
-  const size_t need = bond_smem_bytes(c->chi, c->celt, c->d);
+  const size_t need = bond_smem_bytes(c->chi, c->celt, c->d, c->epp);
   size_t limit = 0;
   cudaError_t el;
   if (c->d == 4)
@@ -3588,6 +3636,7 @@ int env_grid(lt_ctx_s* c) {
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, env_tiled_kernel<double>, LT_BLOCK, 0);
   if (e != cudaSuccess || occ < 1) occ = 2;
   if (occ > 8) occ = 8;
+  if (c->env_occ > 0 && c->env_occ < occ) occ = c->env_occ;  // the schedule's CTAs per SM
   long long g = (long long)occ * c->num_sms;
   const long long cap = env_grid_cap(c->L, c->chi, c->celt, c->num_sms);
   if (g > cap) g = cap;

@@ -72,7 +72,7 @@ uint64_t context_bytes(const lt_config* cfg, int num_sms) {
   b += nt * L * 8 + nt * 8 + nt * 3 * L * 8 + 3 * L * 8;   // density, log weights, rates, rates table
   b += 4 + 64 * 4 + LT_NCOUNTERS * 8 + 8 * nb * d * d * d * d * 16;  // error word, histogram, counters, gates
   b += (2 * L * L + 2 * L) * 8;                            // reduction buffer
-  const uint64_t need = bond_smem_bytes((int)chi, celt, (int)d);
+  const uint64_t need = bond_smem_bytes((int)chi, celt, (int)d, 8);
   if (need > 200 * 1024) b += 2ull * num_sms * need;       // bond scratch when not in shared memory
   uint64_t env_grid = nt < 8ull * num_sms ? nt : 8ull * num_sms;
   const uint64_t cap = (uint64_t)env_grid_cap((int)L, (int)chi, celt, num_sms);
@@ -290,8 +290,12 @@ lt_status lt_server_updates(lt_server s, int64_t id, uint64_t* updates) {
   if (!s || !updates) return LT_ERR_ARG;
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return LT_ERR_ARG;
-  if (it->second.state != 2) return LT_ERR_STATE;
-  *updates = it->second.updates;
+  const Request& r = it->second;
+  *updates = r.updates;
+  if (r.state == 1 && r.ctx) {  // active: the context's counter so far (synchronises its stream)
+    uint64_t cnt[LT_NCOUNTERS] = {0};
+    if (lt_get_counters(r.ctx, cnt, 0) == LT_OK) *updates = cnt[0];
+  }
   return LT_OK;
 }
 

@@ -32,7 +32,8 @@ class lt_config(ctypes.Structure):
         ("gamma_deph", ctypes.c_void_p), ("fermionic_jumps", ctypes.c_int32),
         ("max_sweeps", ctypes.c_int32), ("svd_cut", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("traj_offset", ctypes.c_int64),
-        ("jacobi_tol", ctypes.c_double), ("theta_simt", ctypes.c_int32),
+        ("jacobi_tol", ctypes.c_double), ("theta_path", ctypes.c_int32),
+        ("jacobi_epp", ctypes.c_int32), ("env_ctas_per_sm", ctypes.c_int32),
     ]
 
 
@@ -126,7 +127,8 @@ def _arr(x, L, dtype=np.float64):
 def make_config(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.05,
                 trotter_order=2, gamma_loss=None, gamma_gain=None, gamma_deph=None,
                 fermionic_jumps=1, svd_cut=1e-12, seed=0, traj_offset=0, product_occ=None,
-                method=LT_TRAJ, max_sweeps=0, jacobi_tol=0.0, kraus_dim=0, theta_simt=0):
+                method=LT_TRAJ, max_sweeps=0, jacobi_tol=0.0, kraus_dim=0, theta_path=0,
+                jacobi_epp=0, env_ctas_per_sm=0):
     """An lt_config and the arrays it points to (keep both alive while it is used)."""
     cfg = lt_config()
     cfg.L, cfg.chi_max, cfg.n_traj = L, chi_max, n_traj
@@ -140,7 +142,8 @@ def make_config(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.
     cfg.fermionic_jumps, cfg.svd_cut = int(fermionic_jumps), svd_cut
     cfg.seed, cfg.traj_offset = seed, traj_offset
     cfg.max_sweeps, cfg.jacobi_tol = max_sweeps, jacobi_tol
-    cfg.theta_simt = int(theta_simt)
+    cfg.theta_path, cfg.jacobi_epp = int(theta_path), int(jacobi_epp)
+    cfg.env_ctas_per_sm = int(env_ctas_per_sm)
     return cfg, keep
 
 
@@ -442,7 +445,7 @@ class Server:
         return _lib.lt_server_error(self.h, rid).decode()
 
     def updates(self, rid):
-        """Two-site updates a finished request executed."""
+        """Two-site updates a request executed (so far, while it is active)."""
         u = np.zeros(1, np.uint64)
         _check(_lib.lt_server_updates(self.h, rid, _ptr(u)), "lt_server_updates")
         return int(u[0])
