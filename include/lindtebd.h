@@ -97,19 +97,16 @@ typedef struct {
                              /* schedule's choice, 1 = tensor cores (exact 8-bit   */
                              /* digit products, error below the final rounding),   */
                              /* 2 = single-precision FMAs                          */
-  int32_t jacobi_epp;        /* element pairs per lane of the row-pair Jacobi that  */
-                             /* takes theta wider than 128: 0 = tuned, 4, or 8     */
-                             /* (8 in LT_MIXED only)                               */
   int32_t env_ctas_per_sm;   /* CTAs per SM of the environment kernels (rates and  */
                              /* observables): 0 = tuned, 1..8                      */
 } lt_config;
 
-/* Schedules.  The fields theta_path, jacobi_epp and env_ctas_per_sm left at 0 take
+/* Schedules.  The fields theta_path and env_ctas_per_sm left at 0 take
  * the values of a table the library carries, written by the autotuner
  * (paper_2609_18841_b300/autotune.py) from timings on the device: for each number of
  * values per site (2 or 4), precision and chi_max (the smallest tabulated chi_max at
  * or above the context's), the candidate schedule with the shortest time step.
- * Without an entry: tensor cores, 4 element pairs, up to 8 CTAs per SM. */
+ * Without an entry: tensor cores, up to 8 CTAs per SM. */
 
 /* Create a context: validate cfg, allocate the ensemble on the current device
  * and set every trajectory to the initial product state (Sec. 4.1: the

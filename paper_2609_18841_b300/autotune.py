@@ -2,7 +2,7 @@
 
 For every (values per site, precision, chi_max) of the grid below it times whole time
 steps of an ensemble of synthetic states at full bond dimension under candidate
-schedules (the lt_config fields theta_path, jacobi_epp and env_ctas_per_sm) with CUDA
+schedules (the lt_config fields theta_path and env_ctas_per_sm) with CUDA
 events, by coordinate search from the default schedule, and keeps the fastest.  It
 writes the table as JSON and as the C header the library compiles in
 (csrc/lt_schedule_table.h), which lt_create consults for every field left at 0.
@@ -70,10 +70,8 @@ def tune_one(lt, torch, d, precision, chi, log):
     knobs = []
     if precision == lt.LT_MIXED and d == 2:
         knobs.append(("theta_path", (1, 2)))
-    if precision == lt.LT_MIXED and d * chi > 128:
-        knobs.append(("jacobi_epp", (4, 8)))
     knobs.append(("env_ctas_per_sm", (8, 4, 2, 1)))
-    best = {"theta_path": 1, "jacobi_epp": 4, "env_ctas_per_sm": 8}
+    best = {"theta_path": 1, "env_ctas_per_sm": 8}
     t_default = time_steps(lt, torch, d, precision, chi, best, n_traj, L, steps)
     t_best = t_default
     tried = {json.dumps(best, sort_keys=True): t_default}
@@ -99,14 +97,13 @@ def header(entries, gpu):
              "// from timings on the device (%s); no entry: the defaults of lindtebd.h." % gpu,
              "#pragma once", "", "struct LtSchedule {",
              "  int d, precision, chi_max;          // values per site, lt_precision, chi_max",
-             "  int theta_path, jacobi_epp, env_ctas_per_sm;", "};", "",
+             "  int theta_path, env_ctas_per_sm;", "};", "",
              "static const LtSchedule kLtSchedules[] = {"]
     for e in entries:
         s = e["schedule"]
-        lines.append("    {%d, %d, %d, %d, %d, %d},  // %.1f -> %.1f ms per step" % (
+        lines.append("    {%d, %d, %d, %d, %d},  // %.1f -> %.1f ms per step" % (
             e["d"], 1 if e["precision"] == "mixed" else 0, e["chi_max"], s["theta_path"],
-            s["jacobi_epp"], s["env_ctas_per_sm"], e["ms_per_step_default"],
-            e["ms_per_step_tuned"]))
+            s["env_ctas_per_sm"], e["ms_per_step_default"], e["ms_per_step_tuned"]))
     lines += ["};", ""]
     return "\n".join(lines)
 

@@ -11,7 +11,7 @@
 
 // the tuned schedule of (values per site, precision, chi_max): the entry with the smallest
 // tabulated chi_max at or above the context's
-static void lt_schedule_lookup(int d, int precision, int chi, int* path, int* epp, int* env) {
+static void lt_schedule_lookup(int d, int precision, int chi, int* path, int* env) {
   const LtSchedule* best = nullptr;
   for (const LtSchedule& e : kLtSchedules) {
     if (e.d != d || e.precision != precision || e.chi_max < chi) continue;
@@ -19,7 +19,6 @@ static void lt_schedule_lookup(int d, int precision, int chi, int* path, int* ep
   }
   if (!best) return;
   if (best->theta_path) *path = best->theta_path;
-  if (best->jacobi_epp) *epp = best->jacobi_epp;
   if (best->env_ctas_per_sm) *env = best->env_ctas_per_sm;
 }
 
@@ -415,7 +414,6 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
       !(cfg->svd_cut >= 0.0) || cfg->max_sweeps < 0 || cfg->max_sweeps > 1000 ||
       !(cfg->jacobi_tol >= 0.0 && cfg->jacobi_tol < 1.0) || cfg->init < LT_INIT_VACUUM || cfg->init > LT_INIT_PRODUCT ||
       cfg->theta_path < 0 || cfg->theta_path > 2 ||
-      (cfg->jacobi_epp != 0 && cfg->jacobi_epp != 4 && cfg->jacobi_epp != 8) ||
       cfg->env_ctas_per_sm < 0 || cfg->env_ctas_per_sm > 8 ||
       (cfg->init == LT_INIT_PRODUCT && !cfg->product_occ) || !std::isfinite(cfg->J))
     return LT_ERR_ARG;
@@ -436,14 +434,12 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   c->jacobi_tol = cfg->jacobi_tol;
   {
     // the schedule: explicit fields, else the tuned table's entry, else the defaults
-    int path = 1, epp = 4, env = 0;
+    int path = 1, env = 0;
     lt_schedule_lookup(c->method == LT_MPDO || c->method == LT_PURIFIED ? 4 : 2, cfg->precision,
-                       cfg->chi_max, &path, &epp, &env);
+                       cfg->chi_max, &path, &env);
     if (cfg->theta_path) path = cfg->theta_path;
-    if (cfg->jacobi_epp) epp = cfg->jacobi_epp;
     if (cfg->env_ctas_per_sm) env = cfg->env_ctas_per_sm;
     c->theta_tc = path == 2 ? 0 : 1;
-    c->epp = cfg->precision == LT_MIXED && epp == 8 ? 8 : 4;
     c->env_occ = env;
   }
   c->seed = cfg->seed;

@@ -150,7 +150,6 @@ template <typename R> struct BondArgs {
   long long scratch_stride;
   int use_smem;
   int use_tc;            // mode 0, single precision, D = 2: theta on the tensor cores
-  int epp;               // element pairs per lane of the row-pair Jacobi (4 or 8)
   int max_sweeps;
   double tol;            // Jacobi threshold, 0 = eps sqrt(n) of the working precision
   int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
@@ -240,7 +239,6 @@ struct lt_ctx_s {
   long long bond_scratch_stride;
   int bond_grid, bond_use_smem;
   int theta_tc;     // single precision, D = 2: theta on the tensor cores (digit products)
-  int epp;          // row-pair Jacobi element pairs per lane (4, or 8 in single precision)
   int env_occ;      // environment-kernel CTAs per SM (0: as many as fit, up to 8)
   size_t bond_smem;
 
@@ -283,7 +281,7 @@ cudaError_t launch_reduce_corr(lt_ctx_s* c, double* out);
 cudaError_t launch_convert_in(lt_ctx_s* c, const double* src, long long n, long long dst_off);
 cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long src_off);
 cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev);
-size_t bond_smem_bytes(int chi, size_t celt, int d, int epp);
+size_t bond_smem_bytes(int chi, size_t celt, int d);
 size_t env_scratch_elems(int L, int chi);
 #define LT_ENV_SCRATCH_BYTES (4ull << 30)  // cap of the environment kernels' scratch
 long long env_grid_cap(int L, int chi, size_t celt, int num_sms);

@@ -596,7 +596,7 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
 }
 
 // threads per CTA of the bond kernel per precision (the row-pair Jacobi holds 4 element
-// pairs of each row per lane, or 8 in single precision when the schedule says so)
+// pairs of each row per lane; 8 measured slower in every configuration, spilling)
 template <typename R> struct BondShape;
 template <> struct BondShape<float> { static constexpr int NT = 512; };
 template <> struct BondShape<double> { static constexpr int NT = 256; };
@@ -1744,10 +1744,9 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
 }
 
 template <typename R>
-__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp,
-                                              int epp) {
+__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
   blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64 && nJ <= LT_REG_DIM;
-  const int span = epp == 8 ? 16 * jacobi_span<R, 8>(nJ) : 8 * jacobi_span<R, 4>(nJ);
+  const int span = 8 * jacobi_span<R, 4>(nJ);  // 4 element pairs per lane
   npad = blocked ? (nJ <= 64 ? 64 : 128) : span * ((nJ + span - 1) / span);
   mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
 }
@@ -1789,7 +1788,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     const int nJ = mode == 2 ? chiM : D * chiR;
     bool blocked;
     int npad, mpJ;
-    jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ, a.epp);
+    jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ);
     // two-level Householder preconditioning; the Jacobi then acts on the r x r
     // upper-triangular factor, whose window (mp2 x npad2) can have more rows than
     // the mJ x nJ layout: a wide matrix (nJ > LT_REG_DIM, rows rounded to even)
@@ -1799,7 +1798,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     const int rr = mJ < nJ ? mJ : nJ;
     bool blk2;
     int npad2, mp2;
-    jacobi_layout<R>(rr, rr, blk2, npad2, mp2, a.epp);
+    jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
     const int mpad = mpJ > mp2 ? mpJ : mp2;
     const int mcap = mode == 1 ? (mpad > D * chiL ? mpad : D * chiL) : mpad;
     const int ldp = npad + 2, ld = nJ + 1;
@@ -1886,14 +1885,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
                                    mp2, rr, npad2, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
     } else {
-      // element pairs per lane of the row-pair Jacobi: 4, or 8 in single precision when
-      // the schedule says so (one group then spans twice the columns)
-      if (sizeof(R) == 4 && a.epp == 8) {
-        if (rr > 2 * 8 * 32)
-          sweeps = jacobi_rows<R, 8, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
-        else
-          sweeps = jacobi_rows<R, 8, false>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
-      } else if (rr > 2 * 4 * 32) {
+      if (rr > 2 * 4 * 32) {
         sweeps = jacobi_rows<R, 4, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
       } else {
         sweeps = jacobi_rows<R, 4, false>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
@@ -2022,24 +2014,36 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       __syncthreads();
       const int m = D * chiL;
       const R invn = mode == 0 && !a.keep_norm ? (R)(1.0 / s_norm) : (R)1;
-      const int rq = (m + 3) >> 2;
-      for (int idx = tid; idx < rq * k; idx += blockDim.x) {
-        const int r0 = (idx / k) << 2, j = idx - (idx / k) * k;
-        const Tc* yj = Y + j * ld;
-        Tc acc[4] = {czero<Tc>(), czero<Tc>(), czero<Tc>(), czero<Tc>()};
+      // B_b[r][j] = sum_c theta~[r][c] conj(V_k^+[j][c]): a thread takes four rows and two
+      // columns j, j + 1, so each load of theta~ feeds two products and each load of V_k^+
+      // four
+      const int rq = (m + 3) >> 2, kq = (k + 1) >> 1;
+      for (int idx = tid; idx < rq * kq; idx += blockDim.x) {
+        const int g = idx / kq, r0 = g << 2, j0 = 2 * (idx - g * kq);
+        const bool two = j0 + 1 < k;
+        const Tc* y0 = Y + j0 * ld;
+        const Tc* y1 = Y + (two ? j0 + 1 : j0) * ld;
+        Tc acc[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = czero<Tc>();
         const int nr = m - r0 < 4 ? m - r0 : 4;
         for (int c = 0; c < nJ; ++c) {
-          const Tc yv = yj[c];
+          const Tc v0 = y0[c], v1 = y1[c];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
             if (u < nr) {
               const int o = (r0 + u) * ldp + c;
-              cfmac(acc[u], cmk<Tc>(Xr[o], Xi[o]), yv);
+              const Tc x = cmk<Tc>(Xr[o], Xi[o]);
+              cfmac(acc[u][0], x, v0);
+              cfmac(acc[u][1], x, v1);
             }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u < nr) Bl[(r0 + u) * k + j] = cscale(acc[u], invn);
+          if (u < nr) {
+            Bl[(r0 + u) * k + j0] = cscale(acc[u][0], invn);
+            if (two) Bl[(r0 + u) * k + j0 + 1] = cscale(acc[u][1], invn);
+          }
       }
       for (int idx = tid; idx < k * nJ; idx += blockDim.x) {
         const int j = idx / nJ, c = idx - j * nJ;
@@ -3193,14 +3197,14 @@ inline int grid_for(long long n, int block) {
 }  // namespace
 
 // ---- launchers -------------------------------------------------------------------------------
-size_t bond_smem_bytes(int chi, size_t celt, int d, int epp) {
+size_t bond_smem_bytes(int chi, size_t celt, int d) {
   // Largest workspace of a task, in complex elements, over the three modes with
   // every dimension at chi and d physical values per site (mirrors the layout of
   // bond_update_kernel): the Jacobi matrix planar mcap x (npad + 2), V_k^+
   // k x (nJ + 1), plus the staging of B_{b+1} (mode 0) or of the new site
   // tensors (mode 2).
   const bool single = celt == sizeof(float2);
-  if (!single || epp != 8) epp = 4;
+  const size_t epp = 4;  // element pairs per lane of the row-pair Jacobi
   auto npad_of = [&](size_t m, size_t n) {
     size_t gs = 1;
     while (gs * 2 * epp < n && gs < 32) gs <<= 1;
@@ -3262,8 +3266,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.nb = nb;
   a.gates = gates;
   a.mode = mode;
-  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt, D, c->epp) / c->celt);
-  a.epp = sizeof(R) == 4 && c->epp == 8 ? 8 : 4;
+  a.ws_elems = (long long)(bond_smem_bytes(c->chi, c->celt, D) / c->celt);
   a.L = c->L;
   a.chi = c->chi;
   a.slot = c->slot;
@@ -3542,7 +3545,7 @@ static cudaError_t bond_attributes(size_t limit, size_t smem, int* occ) {
 
 // attribute setup and occupancy for the bond kernel (called once per context)
 cudaError_t configure_bond(lt_ctx_s* c) {
-  const size_t need = bond_smem_bytes(c->chi, c->celt, c->d, c->epp);
+  const size_t need = bond_smem_bytes(c->chi, c->celt, c->d);
   size_t limit = 0;
   cudaError_t el;
   if (c->d == 4)

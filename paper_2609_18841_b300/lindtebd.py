@@ -33,7 +33,7 @@ class lt_config(ctypes.Structure):
         ("max_sweeps", ctypes.c_int32), ("svd_cut", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("traj_offset", ctypes.c_int64),
         ("jacobi_tol", ctypes.c_double), ("theta_path", ctypes.c_int32),
-        ("jacobi_epp", ctypes.c_int32), ("env_ctas_per_sm", ctypes.c_int32),
+        ("env_ctas_per_sm", ctypes.c_int32),
     ]
 
 
@@ -128,7 +128,7 @@ def make_config(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.
                 trotter_order=2, gamma_loss=None, gamma_gain=None, gamma_deph=None,
                 fermionic_jumps=1, svd_cut=1e-12, seed=0, traj_offset=0, product_occ=None,
                 method=LT_TRAJ, max_sweeps=0, jacobi_tol=0.0, kraus_dim=0, theta_path=0,
-                jacobi_epp=0, env_ctas_per_sm=0):
+                env_ctas_per_sm=0):
     """An lt_config and the arrays it points to (keep both alive while it is used)."""
     cfg = lt_config()
     cfg.L, cfg.chi_max, cfg.n_traj = L, chi_max, n_traj
@@ -142,8 +142,7 @@ def make_config(L, chi_max, n_traj, precision=LT_FP64, init="neel", J=1.0, dt=0.
     cfg.fermionic_jumps, cfg.svd_cut = int(fermionic_jumps), svd_cut
     cfg.seed, cfg.traj_offset = seed, traj_offset
     cfg.max_sweeps, cfg.jacobi_tol = max_sweeps, jacobi_tol
-    cfg.theta_path, cfg.jacobi_epp = int(theta_path), int(jacobi_epp)
-    cfg.env_ctas_per_sm = int(env_ctas_per_sm)
+    cfg.theta_path, cfg.env_ctas_per_sm = int(theta_path), int(env_ctas_per_sm)
     return cfg, keep
 
 

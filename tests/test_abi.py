@@ -28,11 +28,10 @@ def test_library_exports_every_declared_symbol():
 
 def test_config_struct_layout_matches_header():
     from paper_2609_18841_b300.lindtebd import lt_config
-    assert ctypes.sizeof(lt_config) == 136
+    assert ctypes.sizeof(lt_config) == 128
     assert lt_config.J.offset == 40 and lt_config.svd_cut.offset == 88
     assert lt_config.traj_offset.offset == 104 and lt_config.jacobi_tol.offset == 112
-    assert lt_config.theta_path.offset == 120 and lt_config.jacobi_epp.offset == 124
-    assert lt_config.env_ctas_per_sm.offset == 128
+    assert lt_config.theta_path.offset == 120 and lt_config.env_ctas_per_sm.offset == 124
 
 
 @pytest.mark.parametrize("kw,status", [
@@ -48,8 +47,8 @@ def test_config_struct_layout_matches_header():
     (dict(method=2, gamma_loss=[0, 0, 0.1, 0, 0, 0, 0, 0]), 7),
     (dict(method=2, gamma_gain=[0, 0, 0, 0, 0, 0, 0.2, 0]), 7),
     (dict(init="product"), 1),
-    # schedules: theta path 0..2, 4 or 8 element pairs, 0..8 CTAs per SM
-    (dict(theta_path=3), 1), (dict(jacobi_epp=6), 1), (dict(env_ctas_per_sm=9), 1),
+    # schedules: theta path 0..2, 0..8 CTAs per SM
+    (dict(theta_path=3), 1), (dict(env_ctas_per_sm=9), 1),
 ])
 def test_invalid_configurations_are_rejected_on_the_host(kw, status):
     from paper_2609_18841_b300 import lindtebd as lt

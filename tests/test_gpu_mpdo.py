@@ -39,14 +39,14 @@ def source_sink(L, chi, g=0.5, deph=0.0, dt=0.05):
     return cfg_of(L, chi, dt=dt, loss=loss, gain=gain, deph=deph, fermionic=True, occ="vacuum")
 
 
-def ensemble(cfg, n, precision, cut=None):
+def ensemble(cfg, n, precision, cut=None, **kw):
     lt = _lt()
     occ = cfg.occupation.astype(np.uint8)
     return lt.Ensemble(cfg.L, cfg.chi_max, n, method=lt.LT_MPDO, precision=precision,
                        init="product", product_occ=occ, J=cfg.J, dt=cfg.dt,
                        gamma_loss=cfg.gamma_loss, gamma_gain=cfg.gamma_gain,
                        gamma_deph=cfg.gamma_deph, fermionic_jumps=int(cfg.fermionic),
-                       svd_cut=cfg.svd_cut if cut is None else cut)
+                       svd_cut=cfg.svd_cut if cut is None else cut, **kw)
 
 
 def close(got, want, tol, what):

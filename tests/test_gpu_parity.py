@@ -29,12 +29,13 @@ def oracle_cfg(w, L=None, chi=None, cut=1e-12, **over):
     return tebd.TrajectoryConfig(L, **d)
 
 
-def gpu_ensemble(cfg, n_traj, precision, init="neel"):
+def gpu_ensemble(cfg, n_traj, precision, init="neel", **kw):
     lt = _lt()
     return lt.Ensemble(cfg.L, cfg.chi_max, n_traj, precision=precision, init=init, J=cfg.J,
                        dt=cfg.dt, trotter_order=cfg.trotter_order, gamma_loss=cfg.gamma_loss,
                        gamma_gain=cfg.gamma_gain, gamma_deph=cfg.gamma_deph,
-                       fermionic_jumps=int(cfg.fermionic), svd_cut=cfg.svd_cut, seed=cfg.seed)
+                       fermionic_jumps=int(cfg.fermionic), svd_cut=cfg.svd_cut, seed=cfg.seed,
+                       **kw)
 
 
 def gpu_steps(ens, cfg, n_steps, replay=None, step0=0):
@@ -89,7 +90,8 @@ def test_w1_fp64_replay(w1_oracle):
     assert_close(dens, res["density"], FP64_TOL, "density")
 
 
-def test_w1_mixed_replay_error_bounds(w1_oracle):
+@pytest.mark.parametrize("theta_path", [1, 2], ids=["theta_tensor_cores", "theta_fma"])
+def test_w1_mixed_replay_error_bounds(w1_oracle, theta_path):
     # mixed: single-precision tensors, theta contractions and Jacobi rotations;
     # double-precision singular values, norms, Schmidt values and rates; the kept
     # right singular vectors re-orthonormalised after the Jacobi and the gates
@@ -97,9 +99,11 @@ def test_w1_mixed_replay_error_bounds(w1_oracle):
     # the 1e-6 ensemble target for <c_i^+ c_j>.  Per trajectory the floor is the
     # single-precision accumulation of the theta contractions (about 3x the
     # rounding of the stored tensors in a CPU emulation of the same steps).
+    # theta_path: theta from exact digit products on the tensor cores (1), or from
+    # single-precision FMAs (2)
     cfg, n, res = w1_oracle
     lt = _lt()
-    with gpu_ensemble(cfg, n, lt.LT_MIXED) as ens:
+    with gpu_ensemble(cfg, n, lt.LT_MIXED, theta_path=theta_path) as ens:
         gpu_steps(ens, cfg, workloads.W1["n_steps"], replay=res["jumps"])
         mean, _, dens = ens.density(per_traj=True)
         C, Cp = ens.corr(per_traj=True)
