@@ -528,7 +528,7 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (st == LT_OK) st = dalloc(c, &c->counters, LT_NCOUNTERS);
   if (st == LT_OK) st = dalloc(c, &c->gates, 8 * nb * (size_t)(c->d * c->d * c->d * c->d));
   if (st == LT_OK) st = dalloc(c, &c->red, 2 * (size_t)L * L + 2 * (size_t)L);
-  if (st == LT_OK && !c->bond_use_smem)
+  if (st == LT_OK && c->bond_scratch_stride > 0)
     st = dalloc(c, (char**)&c->bond_scratch, (size_t)c->bond_grid * c->bond_scratch_stride * c->celt);
   if (st == LT_OK)
     st = dalloc(c, (char**)&c->env_scratch, (size_t)c->env_grid * c->env_scratch_stride * c->celt);

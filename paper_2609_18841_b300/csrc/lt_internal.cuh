@@ -142,13 +142,14 @@ template <typename R> struct BondArgs {
   int bond0, nb;
   const double2* gates;  // [L-1][16] or nullptr = identity
   int mode;              // 0 two-site gate update, 1 shift left, 2 restore bond
-  long long ws_elems;    // workspace capacity in complex elements
+  long long ws_elems;    // largest workspace of a task, in complex elements
   int L, chi, slot;
   double cut;
   int* err;
-  Tc* scratch;           // per-CTA workspace when it does not fit shared memory
+  long long smem_elems;  // dynamic shared memory of the launch, in complex elements: a
+                         // task whose workspace fits works there
+  Tc* scratch;           // per-CTA global workspace of the tasks that do not fit, or nullptr
   long long scratch_stride;
-  int use_smem;
   int use_tc;            // mode 0, single precision, D = 2: theta on the tensor cores
   int max_sweeps;
   double tol;            // Jacobi threshold, 0 = eps sqrt(n) of the working precision
@@ -237,7 +238,7 @@ struct lt_ctx_s {
 
   void* bond_scratch;
   long long bond_scratch_stride;
-  int bond_grid, bond_use_smem;
+  int bond_grid;
   int theta_tc;     // single precision, D = 2: theta on the tensor cores (digit products)
   int env_occ;      // environment-kernel CTAs per SM (0: as many as fit, up to 8)
   size_t bond_smem;

@@ -428,8 +428,20 @@ struct BJRows {
   float nrl;         // squared norm of row (lane & 7) of the eight
 };
 
-template <int CPL, int P0, int Q0, int P1, int Q1, int P2, int Q2, int P3, int Q3>
-__device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any, int& nrot) {
+// Rows longer than a warp's 128 columns: GW warps hold one column slice each of the
+// same eight rows, and the eight partial sums of a sub-round go through shared memory
+// (two buffers used in turn, one named barrier per sub-round) and are added in warp
+// order, so that every warp of the group derives the same rotations.
+struct BJGroup {
+  float* part;  // [2][GW][8]
+  int bar;      // named barrier of the group
+  int wg;       // this warp's slice
+  int buf;      // buffer of the next sub-round
+};
+
+template <int CPL, int GW, int P0, int Q0, int P1, int Q1, int P2, int Q2, int P3, int Q3>
+__device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any, int& nrot,
+                                            BJGroup& grp) {
   const int lane = threadIdx.x & 31;
   const float2 ONE2 = make_float2(1.f, 1.f), MONE2 = make_float2(-1.f, -1.f);
   float v[8];
@@ -474,6 +486,16 @@ __device__ __forceinline__ void bj_subround(BJRows<CPL>& w, float tol, int& any,
     k1 += __shfl_xor_sync(FULL, k1, 2);
     k1 += __shfl_xor_sync(FULL, k1, 1);
     v[0] = k1;
+  }
+  if constexpr (GW > 1) {
+    float* pb = grp.part + grp.buf * (GW * 8);
+    if ((lane & 3) == 0) pb[grp.wg * 8 + (lane >> 2)] = v[0];
+    asm volatile("bar.sync %0, %1;" ::"r"(grp.bar), "r"(GW * 32) : "memory");
+    float sum = pb[lane >> 2];
+#pragma unroll
+    for (int t = 1; t < GW; ++t) sum += pb[t * 8 + (lane >> 2)];
+    v[0] = sum;
+    grp.buf ^= 1;
   }
   // lanes 8k..8k+3 hold gx of pair k, lanes 8k+4..8k+7 its gy
   const float other = __shfl_xor_sync(FULL, v[0], 4);
@@ -526,6 +548,7 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int NB = mp >> 2;  // even
   const float tol = tol_override > 0.0 ? (float)tol_override : FLT_EPSILON * sqrtf((float)n);
+  BJGroup grp{nullptr, 0, 0, 0};
   int nrot = 0;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -565,14 +588,14 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
         }
         if (br == 0) {
           // pairs inside each block: circle method on four rows
-          bj_subround<CPL, 0, 3, 1, 2, 4, 7, 5, 6>(w, tol, any, nrot);
-          bj_subround<CPL, 1, 3, 2, 0, 5, 7, 6, 4>(w, tol, any, nrot);
-          bj_subround<CPL, 2, 3, 0, 1, 6, 7, 4, 5>(w, tol, any, nrot);
+          bj_subround<CPL, 1, 0, 3, 1, 2, 4, 7, 5, 6>(w, tol, any, nrot, grp);
+          bj_subround<CPL, 1, 1, 3, 2, 0, 5, 7, 6, 4>(w, tol, any, nrot, grp);
+          bj_subround<CPL, 1, 2, 3, 0, 1, 6, 7, 4, 5>(w, tol, any, nrot, grp);
         }
-        bj_subround<CPL, 0, 4, 1, 5, 2, 6, 3, 7>(w, tol, any, nrot);
-        bj_subround<CPL, 0, 5, 1, 6, 2, 7, 3, 4>(w, tol, any, nrot);
-        bj_subround<CPL, 0, 6, 1, 7, 2, 4, 3, 5>(w, tol, any, nrot);
-        bj_subround<CPL, 0, 7, 1, 4, 2, 5, 3, 6>(w, tol, any, nrot);
+        bj_subround<CPL, 1, 0, 4, 1, 5, 2, 6, 3, 7>(w, tol, any, nrot, grp);
+        bj_subround<CPL, 1, 0, 5, 1, 6, 2, 7, 3, 4>(w, tol, any, nrot, grp);
+        bj_subround<CPL, 1, 0, 6, 1, 7, 2, 4, 3, 5>(w, tol, any, nrot, grp);
+        bj_subround<CPL, 1, 0, 7, 1, 4, 2, 5, 3, 6>(w, tol, any, nrot, grp);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
@@ -592,6 +615,86 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
     if (!__syncthreads_or(any)) break;
   }
   if (lane == 0 && nrot) atomicAdd(nrot_out, nrot);
+  return sweep + 1;
+}
+
+// Block Jacobi for rows of 128 < n <= 512 columns (single precision, the same
+// rotations and circle-method block order as jacobi_blocked): groups of G warps take
+// a pair of 4-row blocks at a time, warp g of a group the columns [128 g, 128 g + 128)
+// of its eight rows in registers, the inner products summed over the group (BJGroup).
+// The rows stay in the workspace (global scratch for these sizes) between block rounds,
+// so a sweep moves the matrix through the registers NB - 1 times instead of once per
+// row pair.  npad = 128 G columns, mp (a multiple of 8) rows; the window beyond the
+// r x r factor is zero.  part: [NT/32/G][2][G][8] floats of shared memory.
+template <int G>
+__device__ __noinline__ int jacobi_wide(float* Xr, float* Xi, int ldp, int mp, int n, float* nrm, float* part,
+                           int* nrot_out, int max_sweeps, double tol_override) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ngr = nw / G, gid = warp / G, wg = warp - gid * G;
+  const bool active = gid < ngr;
+  const int NB = mp >> 2;  // even
+  const float tol = tol_override > 0.0 ? (float)tol_override : FLT_EPSILON * sqrtf((float)n);
+  BJGroup grp{part + (active ? gid : 0) * 2 * G * 8, 1 + gid, wg, 0};
+  int nrot = 0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    __syncthreads();
+    for (int r = warp; r < mp; r += nw) {
+      float acc = 0.f;
+      for (int c = lane; c < n; c += 32) {
+        const float u = Xr[(long long)r * ldp + c], v = Xi[(long long)r * ldp + c];
+        acc = fmaf(u, u, fmaf(v, v, acc));
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (lane == 0) nrm[r] = acc;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int br = 0; br < NB - 1; ++br) {
+      if (active) {
+        for (int bp = gid; bp < (NB >> 1); bp += ngr) {
+          int A, B;
+          rr_pair(br, bp, NB, A, B);
+          BJRows<2> w;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
+            if (t == (lane & 7)) w.nrl = nrm[row];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const long long o = (long long)row * ldp + 128 * wg + 2 * lane + 64 * j;
+              w.r[t][j] = *reinterpret_cast<const float2*>(Xr + o);
+              w.i[t][j] = *reinterpret_cast<const float2*>(Xi + o);
+            }
+          }
+          if (br == 0) {
+            bj_subround<2, G, 0, 3, 1, 2, 4, 7, 5, 6>(w, tol, any, nrot, grp);
+            bj_subround<2, G, 1, 3, 2, 0, 5, 7, 6, 4>(w, tol, any, nrot, grp);
+            bj_subround<2, G, 2, 3, 0, 1, 6, 7, 4, 5>(w, tol, any, nrot, grp);
+          }
+          bj_subround<2, G, 0, 4, 1, 5, 2, 6, 3, 7>(w, tol, any, nrot, grp);
+          bj_subround<2, G, 0, 5, 1, 6, 2, 7, 3, 4>(w, tol, any, nrot, grp);
+          bj_subround<2, G, 0, 6, 1, 7, 2, 4, 3, 5>(w, tol, any, nrot, grp);
+          bj_subround<2, G, 0, 7, 1, 4, 2, 5, 3, 6>(w, tol, any, nrot, grp);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
+            if (wg == 0 && lane == t) nrm[row] = w.nrl;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const long long o = (long long)row * ldp + 128 * wg + 2 * lane + 64 * j;
+              *reinterpret_cast<float2*>(Xr + o) = w.r[t][j];
+              *reinterpret_cast<float2*>(Xi + o) = w.i[t][j];
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(any)) break;
+  }
+  if (lane == 0 && wg == 0 && nrot) atomicAdd(nrot_out, nrot);
   return sweep + 1;
 }
 
@@ -626,6 +729,7 @@ __device__ __forceinline__ void warp_sum2(R& a, R& b) {
 }
 
 #define LT_QR_CH 8  // entries staged in registers per chunk of a Householder update
+#define LT_QR_EPL (LT_MAX_DIM / 32)  // row entries per lane of the generic LQ update
 
 template <typename R> struct TinyNorm;
 template <> struct TinyNorm<float> { static constexpr float v = 1e-18f; };
@@ -692,58 +796,50 @@ __device__ void qr_precondition(R* Xr, R* Xi, int ldp, int m, int n, int r,
   typedef typename CT<R>::T Tc;
   const int warp = threadIdx.x >> 5;
   __syncthreads();
-  // LQ: H_j from the tail of row j, applied from the right to the rows below;
-  // each thread owns one row (no reductions across threads)
+  // LQ: H_j from the tail of row j, applied from the right to the rows below.  A warp
+  // takes a row at a time, lane l the columns l + 32 u (coalesced), with the row and
+  // the reflector in registers (n <= LT_MAX_DIM = 32 LT_QR_EPL); the inner product is
+  // summed over the warp.
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int off = 0;
   for (int j = 0; j < r; ++j) {
     Tc* e = Vst + off;
     const int len = n - j;
     if (warp == 0) {
       const R bt = make_reflector<R>(Xr, Xi, j * ldp + j, 1, len, e);
-      if ((threadIdx.x & 31) == 0) beta[j] = bt;
+      if (lane == 0) beta[j] = bt;
     }
     __syncthreads();
     const R bt = beta[j];
-    if (bt != (R)0) {
-      const Tc* __restrict__ ev = e;
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+    if (bt != (R)0 && j + 1 + warp < m) {
+      Tc ev[LT_QR_EPL];
+#pragma unroll
+      for (int u = 0; u < LT_QR_EPL; ++u) {
+        const int c = lane + 32 * u;
+        ev[u] = c < len ? e[c] : czero<Tc>();
+      }
+      for (int i = j + 1 + warp; i < m; i += nw) {
         R* __restrict__ xr = Xr + i * ldp + j;
         R* __restrict__ xi = Xi + i * ldp + j;
-        R dr = 0, di = 0;  // d = sum_c x_c conj(e_c), in chunks staged in registers
-        for (int c0 = 0; c0 < len; c0 += LT_QR_CH) {
-          R a[LT_QR_CH], b[LT_QR_CH];
-          Tc w[LT_QR_CH];
+        R a[LT_QR_EPL], b[LT_QR_EPL];
+        R dr = 0, di = 0;  // d = sum_c x_c conj(e_c)
 #pragma unroll
-          for (int u = 0; u < LT_QR_CH; ++u) {
-            const bool in = c0 + u < len;
-            a[u] = in ? xr[c0 + u] : (R)0;
-            b[u] = in ? xi[c0 + u] : (R)0;
-            w[u] = in ? ev[c0 + u] : czero<Tc>();
-          }
-#pragma unroll
-          for (int u = 0; u < LT_QR_CH; ++u) {
-            dr = fma(a[u], w[u].x, fma(b[u], w[u].y, dr));
-            di = fma(b[u], w[u].x, fma(-a[u], w[u].y, di));
-          }
+        for (int u = 0; u < LT_QR_EPL; ++u) {
+          const int c = lane + 32 * u;
+          a[u] = c < len ? xr[c] : (R)0;
+          b[u] = c < len ? xi[c] : (R)0;
+          dr = fma(a[u], ev[u].x, fma(b[u], ev[u].y, dr));
+          di = fma(b[u], ev[u].x, fma(-a[u], ev[u].y, di));
         }
+        warp_sum2(dr, di);
         dr *= bt;
         di *= bt;
-        for (int c0 = 0; c0 < len; c0 += LT_QR_CH) {  // x -= beta d e
-          R a[LT_QR_CH], b[LT_QR_CH];
-          Tc w[LT_QR_CH];
 #pragma unroll
-          for (int u = 0; u < LT_QR_CH; ++u) {
-            const bool in = c0 + u < len;
-            a[u] = in ? xr[c0 + u] : (R)0;
-            b[u] = in ? xi[c0 + u] : (R)0;
-            w[u] = in ? ev[c0 + u] : czero<Tc>();
-          }
-#pragma unroll
-          for (int u = 0; u < LT_QR_CH; ++u) {
-            if (c0 + u < len) {
-              xr[c0 + u] = a[u] - fma(dr, w[u].x, -di * w[u].y);
-              xi[c0 + u] = b[u] - fma(dr, w[u].y, di * w[u].x);
-            }
+        for (int u = 0; u < LT_QR_EPL; ++u) {  // x -= beta d e
+          const int c = lane + 32 * u;
+          if (c < len) {
+            xr[c] = a[u] - fma(dr, ev[u].x, -di * ev[u].y);
+            xi[c] = b[u] - fma(dr, ev[u].y, di * ev[u].x);
           }
         }
       }
@@ -1440,6 +1536,61 @@ __host__ __device__ constexpr int smem_bytes(int kp) { return 8 * 128 * kp * 2 +
 
 }  // namespace tcg
 
+template <typename R>
+__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, bool& wide, int& npad,
+                                              int& mp) {
+  blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64 && nJ <= LT_REG_DIM;
+  wide = sizeof(R) == 4 && mJ >= 32 && nJ > LT_REG_DIM;
+  const int span = 8 * jacobi_span<R, 4>(nJ);  // 4 element pairs per lane
+  npad = blocked ? (nJ <= 64 ? 64 : 128)
+                 : wide ? 128 * ((nJ + 127) / 128) : span * ((nJ + span - 1) / span);
+  // the circle-method pairing needs an even count, the block pairing a multiple of 8
+  mp = blocked || wide ? (mJ + 7) & ~7 : mJ + (mJ & 1);
+}
+
+// Workspace layout of one task (complex elements): the matrix the Jacobi sweeps act
+// on is mJ rows of length nJ; after the two-level Householder preconditioning they act
+// on the r x r triangular factor, whose window (mp2 x npad2) can have more rows than
+// the mJ x nJ layout: a wide matrix (nJ > LT_REG_DIM, rows rounded to even) whose
+// factor takes the blocked layout (rows rounded to 8).  The planes hold both, plus in
+// mode 1 the D chi_{b-1} rows of theta~ formed afterwards; every row below mJ is zero
+// from the formation on.  Behind them: V_k^+ rows,
+// the LQ reflectors before it, and the staging of B_{b+1} (mode 0) or of the new site
+// tensors (mode 2).
+struct TaskLayout {
+  int mJ, nJ, rr, npad, mpJ, npad2, mp2, mpad, mcap, ldp, ld, kmax;
+  bool blocked, wide, blk2, wide2;
+  long long need;
+};
+
+template <typename R, int D>
+__device__ __forceinline__ TaskLayout task_layout(int mode, int chiL, int chiM, int chiR,
+                                                  int chi) {
+  TaskLayout t;
+  t.mJ = mode == 1 ? chiM : D * chiL;
+  t.nJ = mode == 2 ? chiM : D * chiR;
+  jacobi_layout<R>(t.mJ, t.nJ, t.blocked, t.wide, t.npad, t.mpJ);
+  t.rr = t.mJ < t.nJ ? t.mJ : t.nJ;
+  jacobi_layout<R>(t.rr, t.rr, t.blk2, t.wide2, t.npad2, t.mp2);
+  t.mpad = t.mpJ > t.mp2 ? t.mpJ : t.mp2;
+  t.mcap = mode == 1 ? (t.mpad > D * chiL ? t.mpad : D * chiL) : t.mpad;
+  t.ldp = t.npad + 2;
+  t.ld = t.nJ + 1;
+  t.kmax = t.rr < chi ? t.rr : chi;
+  const long long vrows = (long long)t.kmax * t.ld;         // V_k^+
+  const long long stage0 = (long long)chiM * D * chiR;      // B_{b+1} staged in V_k^+'s place
+  const long long stage2 = (long long)t.kmax * (chiL > chiR ? D * chiL : D * chiR);
+  // the r LQ reflectors (n - j entries each) occupy the same region until V_k^+
+  // is assembled; with D = 2 they never exceed the V_k^+ rows, with D = 4 they do
+  const long long r0 = t.rr;
+  const long long refl = r0 * t.nJ - r0 * (r0 - 1) / 2;
+  long long tail = mode == 0 ? (vrows > stage0 ? vrows : stage0)
+                             : vrows + (mode == 2 ? stage2 : 0);
+  if (refl > tail) tail = refl;
+  t.need = (long long)t.mcap * t.ldp + tail;
+  return t;
+}
+
 // Whether a mode-0 task of this shape takes the tensor-core theta: 2 chi_L and 2 chi_R
 // at most 128, chi_M at most 64, its digit planes within the workspace, and (with two
 // column passes) the first pass's theta~ within the slot of site b.
@@ -1690,7 +1841,7 @@ __global__ void __launch_bounds__(512, 1) theta_tc_kernel(BondArgs<float> a) {
   uint32_t phase = 0;
   bool ok = true;
   const long long ntask = (long long)(*a.n_trajs) * a.nb;
-  const long long ws_bytes = a.ws_elems * (long long)sizeof(float2);
+  const long long ws_bytes = a.smem_elems * (long long)sizeof(float2);
   for (long long task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
     const int traj = a.trajs[task / a.nb];
     const int b = a.bond0 + 2 * (int)(task % a.nb);
@@ -1698,7 +1849,10 @@ __global__ void __launch_bounds__(512, 1) theta_tc_kernel(BondArgs<float> a) {
     const int chiL = b == 0 ? 1 : dm[b - 1];
     const int chiM = dm[b];
     const int chiR = b == L - 2 ? 1 : dm[b + 1];
-    if (!theta_tc_fits(chiL, chiM, chiR, a.slot, ws_bytes)) continue;
+    // the bond kernel takes theta~ from this pass exactly for these tasks
+    if (task_layout<float, 2>(0, chiL, chiM, chiR, a.chi).need > a.smem_elems ||
+        !theta_tc_fits(chiL, chiM, chiR, a.slot, ws_bytes))
+      continue;
     if (tid < 16) {
       const double2 g = a.gates[b * 16 + tid];
       const float2 h = make_float2((float)g.x, (float)g.y);
@@ -1743,14 +1897,6 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
   return R * A * B - (A + B) * s1 + s2;
 }
 
-template <typename R>
-__device__ __forceinline__ void jacobi_layout(int mJ, int nJ, bool& blocked, int& npad, int& mp) {
-  blocked = sizeof(R) == 4 && mJ >= 32 && nJ >= 64 && nJ <= LT_REG_DIM;
-  const int span = 8 * jacobi_span<R, 4>(nJ);  // 4 element pairs per lane
-  npad = blocked ? (nJ <= 64 ? 64 : 128) : span * ((nJ + span - 1) / span);
-  mp = blocked ? (mJ + 7) & ~7 : mJ + (mJ & 1);  // the circle-method pairing needs an even count
-}
-
 // D physical values per site: 2 for pure states (trajectories, QSD), 4 for the
 // vectorised density matrix (Eq. MPDO; only mode 0 is launched with D = 4).
 template <typename R, int D>
@@ -1767,15 +1913,14 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
   __shared__ double s_norm, s_wdisc;
   __shared__ R s_beta[LT_MAX_DIM + 1];
   __shared__ Tc s_u[LT_MAX_DIM];
+  __shared__ float s_part[256];  // group sums of the wide Jacobi
 
-  R* W = a.use_smem ? reinterpret_cast<R*>(smem_raw)
-                    : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
   const int L = a.L, chi = a.chi, tid = threadIdx.x, mode = a.mode;
   const long long ntask = (long long)(*a.n_trajs) * a.nb;
   // theta~ formed beforehand on the tensor cores (theta_tc_kernel) for the mode-0 tasks
   // that fit, left over the two site slots
   constexpr bool kTc = sizeof(R) == 4 && D == 2;
-  const bool use_tc = kTc && a.use_tc && a.use_smem;
+  const bool use_tc = kTc && a.use_tc;
   for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
     const int traj = a.trajs[task / a.nb];
     const int b = a.bond0 + 2 * (int)(task % a.nb);
@@ -1783,42 +1928,20 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     const int chiL = b == 0 ? 1 : dm[b - 1];
     const int chiM = dm[b];
     const int chiR = b == L - 2 ? 1 : dm[b + 1];
-    // the matrix the Jacobi sweeps act on: mJ rows of length nJ
-    const int mJ = mode == 1 ? chiM : D * chiL;
-    const int nJ = mode == 2 ? chiM : D * chiR;
-    bool blocked;
-    int npad, mpJ;
-    jacobi_layout<R>(mJ, nJ, blocked, npad, mpJ);
-    // two-level Householder preconditioning; the Jacobi then acts on the r x r
-    // upper-triangular factor, whose window (mp2 x npad2) can have more rows than
-    // the mJ x nJ layout: a wide matrix (nJ > LT_REG_DIM, rows rounded to even)
-    // whose factor takes the blocked layout (rows rounded to 8).  The planes hold
-    // both, plus in mode 1 the D chi_{b-1} rows of theta~ formed afterwards, and
-    // every row below mJ is zero from the formation on.
-    const int rr = mJ < nJ ? mJ : nJ;
-    bool blk2;
-    int npad2, mp2;
-    jacobi_layout<R>(rr, rr, blk2, npad2, mp2);
-    const int mpad = mpJ > mp2 ? mpJ : mp2;
-    const int mcap = mode == 1 ? (mpad > D * chiL ? mpad : D * chiL) : mpad;
-    const int ldp = npad + 2, ld = nJ + 1;
-    const int kmax = mJ < nJ ? (mJ < chi ? mJ : chi) : (nJ < chi ? nJ : chi);
-    // workspace check (complex elements); a task that would overrun is skipped
-    const long long vrows = (long long)kmax * ld;          // V_k^+
-    const long long stage0 = (long long)chiM * D * chiR;   // B_{b+1} staged in V_k^+'s place
-    const long long stage2 = (long long)kmax * (chiL > chiR ? D * chiL : D * chiR);
-    // the r LQ reflectors (n - j entries each) occupy the same region until V_k^+
-    // is assembled; with D = 2 they never exceed the V_k^+ rows, with D = 4 they do
-    const long long r0 = mJ < nJ ? mJ : nJ;
-    const long long refl = r0 * nJ - r0 * (r0 - 1) / 2;
-    long long tail = mode == 0 ? (vrows > stage0 ? vrows : stage0)
-                               : vrows + (mode == 2 ? stage2 : 0);
-    if (refl > tail) tail = refl;
-    const long long need = (long long)mcap * ldp + tail;
-    if (need > a.ws_elems || npad2 > npad) {
+    const TaskLayout lay = task_layout<R, D>(mode, chiL, chiM, chiR, chi);
+    const int mJ = lay.mJ, nJ = lay.nJ, rr = lay.rr, npad = lay.npad, npad2 = lay.npad2;
+    const int mp2 = lay.mp2, mpad = lay.mpad, mcap = lay.mcap, ldp = lay.ldp, ld = lay.ld;
+    const int kmax = lay.kmax;
+    const bool blk2 = lay.blk2;
+    // the workspace: shared memory when the task fits it, else this CTA's global scratch;
+    // a task that fits neither is skipped
+    const bool in_smem = lay.need <= a.smem_elems;
+    if ((!in_smem && (a.scratch == nullptr || lay.need > a.ws_elems)) || npad2 > npad) {
       if (tid == 0) atomicOr(a.err, LT_EBIT_WORKSPACE);
       continue;
     }
+    R* W = in_smem ? reinterpret_cast<R*>(smem_raw)
+                   : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
     Tc* Bl = a.B + ((long long)traj * L + b) * a.slot;
     Tc* Br = Bl + a.slot;
     R* Xr = W;
@@ -1838,8 +1961,8 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     __syncthreads();
     bool tc_task = false;
     if constexpr (kTc) {
-      tc_task = use_tc && mode == 0 &&
-                theta_tc_fits(chiL, chiM, chiR, a.slot, a.ws_elems * (long long)sizeof(Tc));
+      tc_task = use_tc && mode == 0 && in_smem &&
+                theta_tc_fits(chiL, chiM, chiR, a.slot, a.smem_elems * (long long)sizeof(Tc));
     }
     if (tc_task) {
       if constexpr (kTc)
@@ -1884,6 +2007,18 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
         sweeps = jacobi_blocked<2>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
                                    mp2, rr, npad2, reinterpret_cast<float*>(s_nrm), &s_nrot,
                                    a.max_sweeps, a.tol);
+    } else if (lay.wide2) {
+      if constexpr (sizeof(R) == 4) {
+        float* fr = reinterpret_cast<float*>(Xr);
+        float* fi = reinterpret_cast<float*>(Xi);
+        float* fn = reinterpret_cast<float*>(s_nrm);
+        if (npad2 == 256)
+          sweeps = jacobi_wide<2>(fr, fi, ldp, mp2, rr, fn, s_part, &s_nrot, a.max_sweeps, a.tol);
+        else if (npad2 == 384)
+          sweeps = jacobi_wide<3>(fr, fi, ldp, mp2, rr, fn, s_part, &s_nrot, a.max_sweeps, a.tol);
+        else
+          sweeps = jacobi_wide<4>(fr, fi, ldp, mp2, rr, fn, s_part, &s_nrot, a.max_sweeps, a.tol);
+      }
     } else {
       if (rr > 2 * 4 * 32) {
         sweeps = jacobi_rows<R, 4, true>(Xr, Xi, ldp, mp2, rr, s_nrm, &s_nrot, a.max_sweeps, a.tol);
@@ -3209,11 +3344,13 @@ size_t bond_smem_bytes(int chi, size_t celt, int d) {
     size_t gs = 1;
     while (gs * 2 * epp < n && gs < 32) gs <<= 1;
     const bool blk = single && m >= 32 && n >= 64 && n <= LT_REG_DIM;
+    const bool wide = single && m >= 32 && n > LT_REG_DIM;
     const size_t span = 2 * epp * gs;
-    return blk ? (n <= 64 ? (size_t)64 : (size_t)128) : span * ((n + span - 1) / span);
+    return blk ? (n <= 64 ? (size_t)64 : (size_t)128)
+               : wide ? 128 * ((n + 127) / 128) : span * ((n + span - 1) / span);
   };
   auto mp_of = [&](size_t m, size_t n) {
-    return (single && m >= 32 && n >= 64 && n <= LT_REG_DIM) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
+    return (single && m >= 32 && n >= 64) ? ((m + 7) & ~(size_t)7) : m + (m & 1);
   };
   const size_t c2 = (size_t)d * chi, c1 = chi;
   // the LQ reflectors of an m x n matrix (r = min(m, n) of n - j entries) share
@@ -3272,10 +3409,10 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
   a.slot = c->slot;
   a.cut = c->cut;
   a.err = c->err_dev;
+  a.smem_elems = (long long)(c->bond_smem / c->celt);
   a.scratch = reinterpret_cast<typename CT<R>::T*>(c->bond_scratch);
   a.scratch_stride = c->bond_scratch_stride;
-  a.use_smem = c->bond_use_smem;
-  a.use_tc = sizeof(R) == 4 && D == 2 && mode == 0 && c->bond_use_smem && c->theta_tc;
+  a.use_tc = sizeof(R) == 4 && D == 2 && mode == 0 && c->theta_tc;
   a.max_sweeps = c->max_sweeps;
   a.tol = c->jacobi_tol;
   a.sweep_hist = c->sweep_hist;
@@ -3292,8 +3429,7 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
       if (e != cudaSuccess) return e;
     }
   }
-  bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_use_smem ? c->bond_smem : 0,
-                             c->stream>>>(a);
+  bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_smem, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError();
 }
@@ -3555,8 +3691,9 @@ cudaError_t configure_bond(lt_ctx_s* c) {
     el = c->prec == LT_MIXED ? bond_smem_limit<float, 2>(c->device, &limit)
                              : bond_smem_limit<double, 2>(c->device, &limit);
   if (el != cudaSuccess) return el;
-  c->bond_use_smem = need <= limit;
-  c->bond_smem = c->bond_use_smem ? need : 0;
+  // every launch gets shared memory for the tasks that fit it; global scratch is
+  // added for the larger ones when the largest task does not fit
+  c->bond_smem = need <= limit ? need : limit;
   cudaError_t e;
   int occ = 0;
   // The dynamic shared-memory ceiling is a property of the kernel, shared by
@@ -3577,7 +3714,7 @@ cudaError_t configure_bond(lt_ctx_s* c) {
   }
   if (occ < 1) occ = 1;
   c->bond_grid = occ * c->num_sms;
-  c->bond_scratch_stride = c->bond_use_smem ? 0 : (long long)(need / c->celt);
+  c->bond_scratch_stride = need <= limit ? 0 : (long long)(need / c->celt);
   return cudaSuccess;
 }
 
