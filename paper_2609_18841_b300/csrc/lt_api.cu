@@ -336,7 +336,8 @@ template <typename T> lt_status dalloc(lt_ctx_s* c, T** p, size_t n) {
 void free_all(lt_ctx_s* c) {
   void* ptrs[] = {c->B, c->lam, c->dims, c->trunc, c->evolve, c->channel, c->replay,
                   c->active_list, c->jumped_list, c->counts, c->density, c->logw, c->rates, c->gam,
-                  c->err_dev, c->sweep_hist, c->counters, c->gates, c->bond_scratch, c->env_scratch,
+                  c->err_dev, c->sweep_hist, c->counters, c->gates, c->bond_scratch, c->bond_cl_state,
+                  c->env_scratch,
                   c->corr, c->red, c->step_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -369,6 +370,8 @@ const char* lt_status_str(lt_status s) {
 const char* lt_last_error(lt_ctx ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
 
 int64_t lt_launch_count(lt_ctx ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t lt_cluster_launches(lt_ctx ctx) { return ctx ? ctx->cluster_launches : 0; }
 
 lt_status lt_get_sweep_histogram(lt_ctx c, int32_t* hist, int32_t clear) {
   lt_status st = guard(c);
@@ -530,6 +533,10 @@ lt_status lt_create(const lt_config* cfg, void* stream, lt_ctx* out) {
   if (st == LT_OK) st = dalloc(c, &c->red, 2 * (size_t)L * L + 2 * (size_t)L);
   if (st == LT_OK && c->bond_scratch_stride > 0)
     st = dalloc(c, (char**)&c->bond_scratch, (size_t)c->bond_grid * c->bond_scratch_stride * c->celt);
+  // the shared Jacobi state of the clusters, as many as can be resident
+  const int ncl_max = std::max(c->bond_ncl[2], std::max(c->bond_ncl[4], c->bond_ncl[8]));
+  if (st == LT_OK && ncl_max > 0)
+    st = dalloc(c, &c->bond_cl_state, (size_t)ncl_max * LT_CL_STATE);
   if (st == LT_OK)
     st = dalloc(c, (char**)&c->env_scratch, (size_t)c->env_grid * c->env_scratch_stride * c->celt);
   uint8_t* occ_dev = nullptr;

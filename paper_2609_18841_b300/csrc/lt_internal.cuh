@@ -151,6 +151,9 @@ template <typename R> struct BondArgs {
   Tc* scratch;           // per-CTA global workspace of the tasks that do not fit, or nullptr
   long long scratch_stride;
   int use_tc;            // mode 0, single precision, D = 2: theta on the tensor cores
+  int cluster;           // CTAs per thread-block cluster (1: no clusters); a cluster
+                         // shares the Jacobi of each task that works in global scratch
+  float* cl_state;       // per cluster: LT_CL_STATE floats (row norms, flags, rotations)
   int max_sweeps;
   double tol;            // Jacobi threshold, 0 = eps sqrt(n) of the working precision
   int* sweep_hist;       // [64] histogram of Jacobi sweep counts, or nullptr
@@ -239,6 +242,8 @@ struct lt_ctx_s {
   void* bond_scratch;
   long long bond_scratch_stride;
   int bond_grid;
+  int bond_ncl[9];  // clusters of 2, 4, 8 CTAs that can be resident at once (0: none)
+  float* bond_cl_state;
   int theta_tc;     // single precision, D = 2: theta on the tensor cores (digit products)
   int env_occ;      // environment-kernel CTAs per SM (0: as many as fit, up to 8)
   size_t bond_smem;
@@ -252,6 +257,7 @@ struct lt_ctx_s {
 
   long long step_counter;
   long long launches;
+  long long cluster_launches;  // of them, bond launches as thread-block clusters
   // a captured time step (lt_step_graph): its launches read the step from step_dev
   long long* step_dev;
   bool use_step_dev;
@@ -283,6 +289,7 @@ cudaError_t launch_convert_in(lt_ctx_s* c, const double* src, long long n, long 
 cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long src_off);
 cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev);
 size_t bond_smem_bytes(int chi, size_t celt, int d);
+#define LT_CL_STATE (LT_MAX_DIM + 8)  // floats of shared Jacobi state per cluster
 size_t env_scratch_elems(int L, int chi);
 #define LT_ENV_SCRATCH_BYTES (4ull << 30)  // cap of the environment kernels' scratch
 long long env_grid_cap(int L, int chi, size_t celt, int num_sms);

@@ -618,6 +618,28 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
   return sweep + 1;
 }
 
+// ---- thread-block clusters ------------------------------------------------------------
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+__device__ __forceinline__ int cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return (int)r;
+}
+__device__ __forceinline__ int cluster_count() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return (int)r;
+}
+// every thread of every CTA of the cluster; writes before it are visible after it
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 // Block Jacobi for rows of 128 < n <= 512 columns (single precision, the same
 // rotations and circle-method block order as jacobi_blocked): groups of G warps take
 // a pair of 4-row blocks at a time, warp g of a group the columns [128 g, 128 g + 128)
@@ -626,46 +648,66 @@ __device__ int jacobi_blocked(float* Xr, float* Xi, int ldp, int mp, int n, int 
 // so a sweep moves the matrix through the registers NB - 1 times instead of once per
 // row pair.  npad = 128 G columns, mp (a multiple of 8) rows; the window beyond the
 // r x r factor is zero.  part: [NT/32/G][2][G][8] floats of shared memory.
+// With C > 1 the C CTAs of a thread-block cluster share the sweeps: the block pairs of
+// a round are dealt over all their groups, a cluster barrier separates the rounds, the
+// row norms live in global memory (nrm), the rows and norms are read past L1 (another
+// SM may have written them), and cl[0..1] (zero on entry) carry the "any rotation" flag
+// of alternate sweeps, cl[2] the rotation count.  Every CTA of the cluster takes the
+// same number of barriers: the loop bounds and the convergence test are cluster-wide.
 template <int G>
-__device__ __noinline__ int jacobi_wide(float* Xr, float* Xi, int ldp, int mp, int n, float* nrm, float* part,
-                           int* nrot_out, int max_sweeps, double tol_override) {
+__device__ __noinline__ int jacobi_wide(float* Xr, float* Xi, int ldp, int mp, int n, float* nrm,
+                                        float* part, int* nrot_out, int max_sweeps,
+                                        double tol_override, int crank, int C, int* cl) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ngr = nw / G, gid = warp / G, wg = warp - gid * G;
   const bool active = gid < ngr;
+  const bool shared = C > 1;
   const int NB = mp >> 2;  // even
   const float tol = tol_override > 0.0 ? (float)tol_override : FLT_EPSILON * sqrtf((float)n);
   BJGroup grp{part + (active ? gid : 0) * 2 * G * 8, 1 + gid, wg, 0};
+  auto ld = [&](const float* q) { return shared ? __ldcg(q) : *q; };
+  auto ld2 = [&](const float* q) {
+    return shared ? __ldcg(reinterpret_cast<const float2*>(q)) : *reinterpret_cast<const float2*>(q);
+  };
+  auto sync = [&]() {
+    if (shared)
+      cluster_sync();
+    else
+      __syncthreads();
+  };
   int nrot = 0;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    __syncthreads();
-    for (int r = warp; r < mp; r += nw) {
+    sync();
+    for (int r = crank * nw + warp; r < mp; r += C * nw) {
       float acc = 0.f;
       for (int c = lane; c < n; c += 32) {
-        const float u = Xr[(long long)r * ldp + c], v = Xi[(long long)r * ldp + c];
+        const float u = ld(Xr + (long long)r * ldp + c), v = ld(Xi + (long long)r * ldp + c);
         acc = fmaf(u, u, fmaf(v, v, acc));
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
       if (lane == 0) nrm[r] = acc;
     }
-    __syncthreads();
+    sync();
+    // the flag of the sweep before the last was read by every CTA before this barrier
+    if (shared && sweep > 0 && crank == 0 && threadIdx.x == 0) cl[(sweep + 1) & 1] = 0;
     int any = 0;
     for (int br = 0; br < NB - 1; ++br) {
       if (active) {
-        for (int bp = gid; bp < (NB >> 1); bp += ngr) {
+        for (int bp = crank * ngr + gid; bp < (NB >> 1); bp += C * ngr) {
           int A, B;
           rr_pair(br, bp, NB, A, B);
           BJRows<2> w;
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int row = t < 4 ? 4 * A + t : 4 * B + (t - 4);
-            if (t == (lane & 7)) w.nrl = nrm[row];
+            if (t == (lane & 7)) w.nrl = ld(nrm + row);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
               const long long o = (long long)row * ldp + 128 * wg + 2 * lane + 64 * j;
-              w.r[t][j] = *reinterpret_cast<const float2*>(Xr + o);
-              w.i[t][j] = *reinterpret_cast<const float2*>(Xi + o);
+              w.r[t][j] = ld2(Xr + o);
+              w.i[t][j] = ld2(Xi + o);
             }
           }
           if (br == 0) {
@@ -690,12 +732,52 @@ __device__ __noinline__ int jacobi_wide(float* Xr, float* Xi, int ldp, int mp, i
           }
         }
       }
-      __syncthreads();
+      sync();
     }
-    if (!__syncthreads_or(any)) break;
+    int more = __syncthreads_or(any);
+    if (shared) {
+      if (threadIdx.x == 0 && more) atomicOr(cl + (sweep & 1), 1);
+      __threadfence();
+      cluster_sync();
+      more = __ldcg(cl + (sweep & 1));
+    }
+    if (!more) break;
   }
-  if (lane == 0 && wg == 0 && nrot) atomicAdd(nrot_out, nrot);
+  if (lane == 0 && wg == 0 && nrot) atomicAdd(shared ? cl + 2 : nrot_out, nrot);
   return sweep + 1;
+}
+
+// The wide Jacobi of one task, by one CTA (C = 1) or shared by the C CTAs of a cluster
+// (cl: the cluster's LT_CL_STATE floats in global memory: row norms, then the flags and
+// the rotation count).  The cluster variant starts and ends with a cluster barrier, so
+// that rank 0's preconditioned factor is visible to all before the sweeps and every row
+// to rank 0 after them; rank 0 adds the cluster's rotations to *nrot.
+__device__ __noinline__ int wide_jacobi(float* Xr, float* Xi, int ldp, int mp, int n, int npad,
+                                        float* s_nrm, float* part, int* nrot, int max_sweeps,
+                                        double tol, int C, int crank, float* cl_state) {
+  float* nrm = s_nrm;
+  int* cl = nullptr;
+  if (C > 1) {
+    nrm = cl_state;
+    cl = reinterpret_cast<int*>(cl_state + LT_MAX_DIM);
+    if (crank == 0 && threadIdx.x == 0) cl[0] = cl[1] = cl[2] = 0;
+    __threadfence();
+    cluster_sync();
+  }
+  int sweeps;
+  if (npad == 256)
+    sweeps = jacobi_wide<2>(Xr, Xi, ldp, mp, n, nrm, part, nrot, max_sweeps, tol, crank, C, cl);
+  else if (npad == 384)
+    sweeps = jacobi_wide<3>(Xr, Xi, ldp, mp, n, nrm, part, nrot, max_sweeps, tol, crank, C, cl);
+  else
+    sweeps = jacobi_wide<4>(Xr, Xi, ldp, mp, n, nrm, part, nrot, max_sweeps, tol, crank, C, cl);
+  if (C > 1) {
+    __threadfence();
+    cluster_sync();
+    __threadfence();
+    if (crank == 0 && threadIdx.x == 0) *nrot += __ldcg(cl + 2);
+  }
+  return sweeps;
 }
 
 // threads per CTA of the bond kernel per precision (the row-pair Jacobi holds 4 element
@@ -729,7 +811,6 @@ __device__ __forceinline__ void warp_sum2(R& a, R& b) {
 }
 
 #define LT_QR_CH 8  // entries staged in registers per chunk of a Householder update
-#define LT_QR_EPL (LT_MAX_DIM / 32)  // row entries per lane of the generic LQ update
 
 template <typename R> struct TinyNorm;
 template <> struct TinyNorm<float> { static constexpr float v = 1e-18f; };
@@ -790,56 +871,111 @@ __device__ __forceinline__ R make_reflector(R* Xr, R* Xi, int base, int st, int 
   return tiny ? (R)0 : (R)2 / (2 * alpha * (alpha + ax0));
 }
 
+// One LQ step on rows j+1..m-1 of a wide matrix: a warp takes a row at a time, lane l
+// the columns l + 32 u (coalesced), with the row and the reflector e (len <= 32 EPL
+// entries) in registers; the inner product is summed over the warp.
+template <typename R, int EPL>
+__device__ __forceinline__ void lq_update_warp(R* Xr, R* Xi, int ldp, int m, int j, int len,
+                                               const typename CT<R>::T* e, R bt) {
+  typedef typename CT<R>::T Tc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (j + 1 + warp >= m) return;
+  Tc ev[EPL];
+#pragma unroll
+  for (int u = 0; u < EPL; ++u) {
+    const int c = lane + 32 * u;
+    ev[u] = c < len ? e[c] : czero<Tc>();
+  }
+  for (int i = j + 1 + warp; i < m; i += nw) {
+    R* __restrict__ xr = Xr + (long long)i * ldp + j;
+    R* __restrict__ xi = Xi + (long long)i * ldp + j;
+    R a[EPL], b[EPL];
+    R dr = 0, di = 0;  // d = sum_c x_c conj(e_c)
+#pragma unroll
+    for (int u = 0; u < EPL; ++u) {
+      const int c = lane + 32 * u;
+      a[u] = c < len ? xr[c] : (R)0;
+      b[u] = c < len ? xi[c] : (R)0;
+      dr = fma(a[u], ev[u].x, fma(b[u], ev[u].y, dr));
+      di = fma(b[u], ev[u].x, fma(-a[u], ev[u].y, di));
+    }
+    warp_sum2(dr, di);
+    dr *= bt;
+    di *= bt;
+#pragma unroll
+    for (int u = 0; u < EPL; ++u) {  // x -= beta d e
+      const int c = lane + 32 * u;
+      if (c < len) {
+        xr[c] = a[u] - fma(dr, ev[u].x, -di * ev[u].y);
+        xi[c] = b[u] - fma(dr, ev[u].y, di * ev[u].x);
+      }
+    }
+  }
+}
+
 template <typename R>
 __device__ void qr_precondition(R* Xr, R* Xi, int ldp, int m, int n, int r,
                                 typename CT<R>::T* Vst, R* beta, typename CT<R>::T* su) {
   typedef typename CT<R>::T Tc;
   const int warp = threadIdx.x >> 5;
   __syncthreads();
-  // LQ: H_j from the tail of row j, applied from the right to the rows below.  A warp
-  // takes a row at a time, lane l the columns l + 32 u (coalesced), with the row and
-  // the reflector in registers (n <= LT_MAX_DIM = 32 LT_QR_EPL); the inner product is
-  // summed over the warp.
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // LQ: H_j from the tail of row j, applied from the right to the rows below.  Rows of
+  // up to 128 columns: a thread owns a row (no reductions across threads); longer rows
+  // (global scratch): a warp takes a row at a time, coalesced (lq_update_warp)
   int off = 0;
   for (int j = 0; j < r; ++j) {
     Tc* e = Vst + off;
     const int len = n - j;
     if (warp == 0) {
       const R bt = make_reflector<R>(Xr, Xi, j * ldp + j, 1, len, e);
-      if (lane == 0) beta[j] = bt;
+      if ((threadIdx.x & 31) == 0) beta[j] = bt;
     }
     __syncthreads();
     const R bt = beta[j];
-    if (bt != (R)0 && j + 1 + warp < m) {
-      Tc ev[LT_QR_EPL];
-#pragma unroll
-      for (int u = 0; u < LT_QR_EPL; ++u) {
-        const int c = lane + 32 * u;
-        ev[u] = c < len ? e[c] : czero<Tc>();
-      }
-      for (int i = j + 1 + warp; i < m; i += nw) {
+    if (bt != (R)0 && n > 256) {
+      lq_update_warp<R, 16>(Xr, Xi, ldp, m, j, len, e, bt);
+    } else if (bt != (R)0 && n > 128) {
+      lq_update_warp<R, 8>(Xr, Xi, ldp, m, j, len, e, bt);
+    } else if (bt != (R)0) {
+      const Tc* __restrict__ ev = e;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
         R* __restrict__ xr = Xr + i * ldp + j;
         R* __restrict__ xi = Xi + i * ldp + j;
-        R a[LT_QR_EPL], b[LT_QR_EPL];
-        R dr = 0, di = 0;  // d = sum_c x_c conj(e_c)
+        R dr = 0, di = 0;  // d = sum_c x_c conj(e_c), in chunks staged in registers
+        for (int c0 = 0; c0 < len; c0 += LT_QR_CH) {
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
 #pragma unroll
-        for (int u = 0; u < LT_QR_EPL; ++u) {
-          const int c = lane + 32 * u;
-          a[u] = c < len ? xr[c] : (R)0;
-          b[u] = c < len ? xi[c] : (R)0;
-          dr = fma(a[u], ev[u].x, fma(b[u], ev[u].y, dr));
-          di = fma(b[u], ev[u].x, fma(-a[u], ev[u].y, di));
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const bool in = c0 + u < len;
+            a[u] = in ? xr[c0 + u] : (R)0;
+            b[u] = in ? xi[c0 + u] : (R)0;
+            w[u] = in ? ev[c0 + u] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            dr = fma(a[u], w[u].x, fma(b[u], w[u].y, dr));
+            di = fma(b[u], w[u].x, fma(-a[u], w[u].y, di));
+          }
         }
-        warp_sum2(dr, di);
         dr *= bt;
         di *= bt;
+        for (int c0 = 0; c0 < len; c0 += LT_QR_CH) {  // x -= beta d e
+          R a[LT_QR_CH], b[LT_QR_CH];
+          Tc w[LT_QR_CH];
 #pragma unroll
-        for (int u = 0; u < LT_QR_EPL; ++u) {  // x -= beta d e
-          const int c = lane + 32 * u;
-          if (c < len) {
-            xr[c] = a[u] - fma(dr, ev[u].x, -di * ev[u].y);
-            xi[c] = b[u] - fma(dr, ev[u].y, di * ev[u].x);
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            const bool in = c0 + u < len;
+            a[u] = in ? xr[c0 + u] : (R)0;
+            b[u] = in ? xi[c0 + u] : (R)0;
+            w[u] = in ? ev[c0 + u] : czero<Tc>();
+          }
+#pragma unroll
+          for (int u = 0; u < LT_QR_CH; ++u) {
+            if (c0 + u < len) {
+              xr[c0 + u] = a[u] - fma(dr, w[u].x, -di * w[u].y);
+              xi[c0 + u] = b[u] - fma(dr, w[u].y, di * w[u].x);
+            }
           }
         }
       }
@@ -1897,9 +2033,37 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
   return R * A * B - (A + B) * s1 + s2;
 }
 
+// The CTAs of rank > 0 of a cluster: they walk the tasks of their cluster like rank 0
+// and join exactly the Jacobis that rank 0 shares (tasks in global scratch with rows
+// of more than 128 columns); everything else of a task is rank 0's.
+template <int D>
+__device__ __noinline__ void cluster_helper(const BondArgs<float>& a, float* s_nrm, float* s_part,
+                                           int* s_nrot) {
+  const int C = a.cluster, crank = cluster_rank(), L = a.L;
+  const long long cid = cluster_index(), ncid = cluster_count();
+  const long long ntask = (long long)(*a.n_trajs) * a.nb;
+  for (long long task = cid; task < ntask; task += ncid) {
+    const int traj = a.trajs[task / a.nb];
+    const int b = a.bond0 + 2 * (int)(task % a.nb);
+    const int* dm = a.dims + (long long)traj * (L - 1);
+    const int chiL = b == 0 ? 1 : dm[b - 1];
+    const int chiM = dm[b];
+    const int chiR = b == L - 2 ? 1 : dm[b + 1];
+    const TaskLayout lay = task_layout<float, D>(a.mode, chiL, chiM, chiR, a.chi);
+    const bool in_smem = lay.need <= a.smem_elems;
+    if ((!in_smem && (a.scratch == nullptr || lay.need > a.ws_elems)) || lay.npad2 > lay.npad)
+      continue;
+    if (in_smem || !lay.wide2) continue;
+    float* W = reinterpret_cast<float*>(a.scratch + cid * C * a.scratch_stride);
+    wide_jacobi(W, W + (long long)lay.mcap * lay.ldp, lay.ldp, lay.mp2, lay.rr, lay.npad2, s_nrm,
+                s_part, s_nrot, a.max_sweeps, a.tol, C, crank, a.cl_state + cid * LT_CL_STATE);
+  }
+}
+
 // D physical values per site: 2 for pure states (trajectories, QSD), 4 for the
-// vectorised density matrix (Eq. MPDO; only mode 0 is launched with D = 4).
-template <typename R, int D>
+// vectorised density matrix (Eq. MPDO; only mode 0 is launched with D = 4).  CL: the
+// instance launched in thread-block clusters (single precision, a.cluster CTAs each).
+template <typename R, int D, bool CL>
 __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondArgs<R> a) {
   typedef typename CT<R>::T Tc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1921,7 +2085,20 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
   // that fit, left over the two site slots
   constexpr bool kTc = sizeof(R) == 4 && D == 2;
   const bool use_tc = kTc && a.use_tc;
-  for (long long task = blockIdx.x; task < ntask; task += gridDim.x) {
+  // thread-block clusters (single precision): every CTA of a cluster walks the same
+  // tasks; rank 0 works a task alone, except that the whole cluster shares the Jacobi
+  // of a task in global scratch
+  constexpr bool kCl = CL && sizeof(R) == 4;
+  const int C = kCl ? a.cluster : 1;
+  if constexpr (kCl) {
+    if (cluster_rank() != 0) {
+      cluster_helper<D>(a, s_nrm, s_part, &s_nrot);
+      return;
+    }
+  }
+  const long long cid = kCl ? cluster_index() : blockIdx.x;
+  const long long ncid = kCl ? cluster_count() : gridDim.x;
+  for (long long task = cid; task < ntask; task += ncid) {
     const int traj = a.trajs[task / a.nb];
     const int b = a.bond0 + 2 * (int)(task % a.nb);
     const int* dm = a.dims + (long long)traj * (L - 1);
@@ -1940,8 +2117,12 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       if (tid == 0) atomicOr(a.err, LT_EBIT_WORKSPACE);
       continue;
     }
+    // the cluster shares the Jacobi of a task in global scratch (the helper CTAs make
+    // the same decision from the same dimensions in cluster_helper)
+    const bool shared_jac = kCl && C > 1 && !in_smem && lay.wide2;
+    const long long slot_cta = kCl ? cid * C : blockIdx.x;
     R* W = in_smem ? reinterpret_cast<R*>(smem_raw)
-                   : reinterpret_cast<R*>(a.scratch + (long long)blockIdx.x * a.scratch_stride);
+                   : reinterpret_cast<R*>(a.scratch + slot_cta * a.scratch_stride);
     Tc* Bl = a.B + ((long long)traj * L + b) * a.slot;
     Tc* Br = Bl + a.slot;
     R* Xr = W;
@@ -1964,6 +2145,8 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       tc_task = use_tc && mode == 0 && in_smem &&
                 theta_tc_fits(chiL, chiM, chiR, a.slot, a.smem_elems * (long long)sizeof(Tc));
     }
+    // register paths for the sizes they hold (every task up to chi_max = 64)
+    const bool reg = sizeof(R) == 4 && mJ <= LT_REG_DIM && nJ <= LT_REG_DIM && kmax <= LT_REG_CHI;
     if (tc_task) {
       if constexpr (kTc)
         theta_tc_planes(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, npad,
@@ -1985,8 +2168,6 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
         Xi[r * ldp + c] = v.y;
       }
     }
-    // register paths for the sizes they hold (every task up to chi_max = 64)
-    const bool reg = sizeof(R) == 4 && mJ <= LT_REG_DIM && nJ <= LT_REG_DIM && kmax <= LT_REG_CHI;
     if constexpr (sizeof(R) == 4) {
       if (reg)
         qr_precondition_reg<BondShape<R>::NT / LT_REG_DIM>(
@@ -1997,7 +2178,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     } else {
       qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
     }
-    int sweeps;
+    int sweeps = 0;
     if (blk2) {
       if (npad2 == 64)
         sweeps = jacobi_blocked<1>(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp,
@@ -2009,15 +2190,10 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
                                    a.max_sweeps, a.tol);
     } else if (lay.wide2) {
       if constexpr (sizeof(R) == 4) {
-        float* fr = reinterpret_cast<float*>(Xr);
-        float* fi = reinterpret_cast<float*>(Xi);
-        float* fn = reinterpret_cast<float*>(s_nrm);
-        if (npad2 == 256)
-          sweeps = jacobi_wide<2>(fr, fi, ldp, mp2, rr, fn, s_part, &s_nrot, a.max_sweeps, a.tol);
-        else if (npad2 == 384)
-          sweeps = jacobi_wide<3>(fr, fi, ldp, mp2, rr, fn, s_part, &s_nrot, a.max_sweeps, a.tol);
-        else
-          sweeps = jacobi_wide<4>(fr, fi, ldp, mp2, rr, fn, s_part, &s_nrot, a.max_sweeps, a.tol);
+        sweeps = wide_jacobi(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mp2,
+                             rr, npad2, reinterpret_cast<float*>(s_nrm), s_part, &s_nrot,
+                             a.max_sweeps, a.tol, shared_jac ? C : 1, 0,
+                             shared_jac ? a.cl_state + cid * LT_CL_STATE : nullptr);
       }
     } else {
       if (rr > 2 * 4 * 32) {
@@ -3429,9 +3605,47 @@ static cudaError_t launch_bond_t(lt_ctx_s* c, const int* trajs, const int* n_tra
       if (e != cudaSuccess) return e;
     }
   }
-  bond_update_kernel<R, D><<<c->bond_grid, BondShape<R>::NT, c->bond_smem, c->stream>>>(a);
-  c->launches++;
-  return cudaGetLastError();
+  // A launch of few tasks that may need global scratch (single precision, mode 0) gives
+  // each task a cluster of C CTAs, which share its Jacobi: the largest C for which every
+  // task's cluster can be resident at once.
+  a.cluster = 1;
+  a.cl_state = c->bond_cl_state;
+  if constexpr (sizeof(R) == 4) {
+    const long long ntask = (long long)c->n_traj * nb;
+    int C = 1;
+    if (mode == 0 && c->bond_scratch_stride > 0 && c->bond_cl_state)
+      for (int cs = 8; cs >= 2 && C == 1; cs >>= 1)
+        if (c->bond_ncl[cs] >= ntask) C = cs;
+    if (C == 1) {
+      bond_update_kernel<R, D, false><<<c->bond_grid, BondShape<R>::NT, c->bond_smem,
+                                        c->stream>>>(a);
+      c->launches++;
+      return cudaGetLastError();
+    }
+    a.cluster = C;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(C * ntask));
+    cfg.blockDim = dim3(BondShape<R>::NT);
+    cfg.dynamicSmemBytes = c->bond_smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, bond_update_kernel<R, D, true>, a);
+    c->launches++;
+    c->cluster_launches++;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  } else {
+    bond_update_kernel<R, D, false><<<c->bond_grid, BondShape<R>::NT, c->bond_smem,
+                                      c->stream>>>(a);
+    c->launches++;
+    return cudaGetLastError();
+  }
 }
 
 cudaError_t launch_bond(lt_ctx_s* c, const int* trajs, const int* n_trajs, int bond0, int nb,
@@ -3660,23 +3874,60 @@ cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev) {
 template <typename R, int D>
 static cudaError_t bond_smem_limit(int device, size_t* limit) {
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, bond_update_kernel<R, D>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, bond_update_kernel<R, D, false>);
   if (e != cudaSuccess) return e;
+  size_t stat = fa.sharedSizeBytes;
+  if constexpr (sizeof(R) == 4) {
+    e = cudaFuncGetAttributes(&fa, bond_update_kernel<R, D, true>);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes > stat) stat = fa.sharedSizeBytes;
+  }
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (e != cudaSuccess) return e;
-  const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  const size_t room = (size_t)optin > stat ? (size_t)optin - stat : 0;
   *limit = room < (size_t)200 * 1024 ? room : (size_t)200 * 1024;
   return cudaSuccess;
 }
 
 template <typename R, int D>
 static cudaError_t bond_attributes(size_t limit, size_t smem, int* occ) {
-  cudaError_t e = cudaFuncSetAttribute(bond_update_kernel<R, D>,
+  cudaError_t e = cudaFuncSetAttribute(bond_update_kernel<R, D, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bond_update_kernel<R, D>,
+  if constexpr (sizeof(R) == 4) {
+    e = cudaFuncSetAttribute(bond_update_kernel<R, D, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bond_update_kernel<R, D, false>,
                                                        BondShape<R>::NT, smem);
+}
+
+// How many clusters of 2, 4 and 8 CTAs of the cluster instance fit on the device at
+// once with this context's shared memory (0 where none does, or the query fails).
+template <int D>
+static void bond_clusters(lt_ctx_s* c) {
+  for (int cs = 2; cs <= 8; cs <<= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(cs * (c->num_sms / cs)));
+    cfg.blockDim = dim3(BondShape<float>::NT);
+    cfg.dynamicSmemBytes = c->bond_smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, bond_update_kernel<float, D, true>, &cfg) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    c->bond_ncl[cs] = n;
+  }
 }
 
 // attribute setup and occupancy for the bond kernel (called once per context)
@@ -3715,6 +3966,12 @@ cudaError_t configure_bond(lt_ctx_s* c) {
   if (occ < 1) occ = 1;
   c->bond_grid = occ * c->num_sms;
   c->bond_scratch_stride = need <= limit ? 0 : (long long)(need / c->celt);
+  if (c->prec == LT_MIXED && c->bond_scratch_stride > 0) {
+    if (c->d == 4)
+      bond_clusters<4>(c);
+    else
+      bond_clusters<2>(c);
+  }
   return cudaSuccess;
 }
 

@@ -73,7 +73,10 @@ uint64_t context_bytes(const lt_config* cfg, int num_sms) {
   b += 4 + 64 * 4 + LT_NCOUNTERS * 8 + 8 * nb * d * d * d * d * 16;  // error word, histogram, counters, gates
   b += (2 * L * L + 2 * L) * 8;                            // reduction buffer
   const uint64_t need = bond_smem_bytes((int)chi, celt, (int)d);
-  if (need > 200 * 1024) b += 2ull * num_sms * need;       // bond scratch when not in shared memory
+  if (need > 200 * 1024) {
+    b += 2ull * num_sms * need;                              // bond scratch when not in shared memory
+    if (celt == 8) b += (uint64_t)num_sms / 2 * LT_CL_STATE * 4;  // cluster Jacobi state
+  }
   uint64_t env_grid = nt < 8ull * num_sms ? nt : 8ull * num_sms;
   const uint64_t cap = (uint64_t)env_grid_cap((int)L, (int)chi, celt, num_sms);
   if (env_grid > cap) env_grid = cap;

@@ -40,7 +40,7 @@ class lt_config(ctypes.Structure):
 EXPORTS = ["lt_create", "lt_destroy", "lt_apply_layer", "lt_apply_jumps", "lt_apply_noise",
            "lt_apply_kraus", "lt_get_log_weights",
            "lt_step", "lt_step_graph", "lt_gates", "lt_measure_density", "lt_measure_corr", "lt_get_stats", "lt_set_state",
-           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_stream", "lt_get_step", "lt_pipe_peaks",
+           "lt_get_state", "lt_save", "lt_load", "lt_get_sweep_histogram", "lt_get_counters", "lt_measure_density_noalloc", "lt_launch_count", "lt_cluster_launches", "lt_stream", "lt_get_step", "lt_pipe_peaks",
            "lt_status_str", "lt_last_error", "lt_context_bytes", "lt_admit_plan",
            "lt_server_create", "lt_server_destroy", "lt_server_submit", "lt_server_tick",
            "lt_server_result", "lt_server_error", "lt_server_usage", "lt_server_updates"]
@@ -73,6 +73,7 @@ def load_library(path=LIB_PATH):
         "lt_get_counters": ([P, P, I32], I32),
         "lt_measure_density_noalloc": ([I32, I32, I32, I32, P, P, P, P], I32),
         "lt_launch_count": ([P], I64),
+        "lt_cluster_launches": ([P], I64),
         "lt_pipe_peaks": ([P], I32),
         "lt_stream": ([P], P),
         "lt_get_step": ([P], I64),
@@ -287,6 +288,10 @@ def lt_pipe_peaks():
 
 def lt_launch_count(ctx):
     return int(_lib.lt_launch_count(ctx))
+
+
+def lt_cluster_launches(ctx):
+    return int(_lib.lt_cluster_launches(ctx))
 
 
 def lt_stream(ctx):

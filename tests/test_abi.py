@@ -71,6 +71,7 @@ def test_status_strings_and_null_context():
     assert lt._lib.lt_step_graph(None, 1) == lt.LT_ERR_ARG
     assert lt._lib.lt_apply_kraus(None) == lt.LT_ERR_ARG
     assert lt._lib.lt_launch_count(None) == 0
+    assert lt._lib.lt_cluster_launches(None) == 0
     out = ctypes.c_void_p(1)
     assert lt._lib.lt_create(None, None, ctypes.byref(out)) == lt.LT_ERR_ARG
     assert out.value is None

@@ -265,8 +265,10 @@ def test_mpdo_edges(name, cfg, steps):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
 def test_configured_chi128_theta_512(precision, tol):
     # chi_max = 128, the vectorised density matrix's configured bond dimension: bond 4
-    # of a 10-site chain with dims 128 | 128 | 128 has theta 512 x 512 (rows longer than
-    # one Jacobi group's span, handled in chunks); bond 2 is 64 x 512.  Synthetic state.
+    # of a 10-site chain with dims 128 | 128 | 128 has theta 512 x 512 (in FP64 rows
+    # longer than one Jacobi group's span, handled in chunks; in single precision the
+    # wide block Jacobi, shared by a thread-block cluster since one chain has few
+    # tasks); bond 2 is 64 x 512.  Synthetic state.
     from paper_2609_18841_b300.lindtebd import unpack_state
     lt = _lt()
     L, chi = 10, 128
@@ -291,3 +293,30 @@ def test_configured_chi128_theta_512(precision, tol):
         assert err < tol, "bond %d: relative error %.2e" % (b, err)
     if precision == "fp64":
         assert list(gd[0]) == ref.bond_dims()
+
+
+@pytest.mark.parametrize("chi", [64, 96, 128])
+def test_cluster_launch_equals_the_one_cta_launch(chi):
+    # One chain gives a layer few tasks, so its single-precision layers go out as
+    # thread-block clusters whose CTAs share the wide Jacobi (theta 4 chi x 4 chi = 256,
+    # 384, 512: warp groups of 2, 3, 4 slices); the same chain inside an ensemble of 96
+    # chains takes one CTA per task.  Both run the same block rounds with the same
+    # arithmetic, so the results must agree bit for bit.
+    lt = _lt()
+    L = 10
+    dims = [4, 16, 64, chi, chi, chi, 64, 16, 4]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=19, d=4, dims=dims)
+    cfg = cfg_of(L, chi, loss=0.1, gain=0.05, cut=1e-6)
+    runs = []
+    for n in (1, 96):
+        with ensemble(cfg, n, lt.LT_MIXED) as e:
+            e.set_state(0, [(B, lam, dims)] * n)
+            e.apply_layer(0, 0.02)
+            e.apply_layer(1, 0.02)
+            runs.append((e.get_state(0, 1), lt.lt_cluster_launches(e.ctx)))
+    (d1, l1, b1), c1 = runs[0]
+    (d2, l2, b2), c2 = runs[1]
+    assert c1 == 2 and c2 == 0
+    assert np.array_equal(d1, d2)
+    assert np.array_equal(l1, l2)
+    assert np.array_equal(b1, b2)

@@ -483,3 +483,29 @@ def test_chi256_theta_512(precision, tol):
         assert err < tol, "bond %d: relative error %.2e" % (b, err)
     if precision == "fp64":
         assert list(gd[0]) == ref.bond_dims()
+
+
+@pytest.mark.parametrize("chi", [128, 256])
+def test_cluster_launch_equals_the_one_cta_launch_pure_state(chi):
+    # One 18-site trajectory at chi_max = 128 or 256 (theta up to 256 or 512) gives a
+    # layer 9 tasks: its single-precision layers go out as thread-block clusters that
+    # share the wide Jacobi; within 16 trajectories (144 tasks) each task has one CTA.
+    # Same block rounds, same arithmetic: equal bit for bit.
+    lt = _lt()
+    L = 18
+    dims = [min(2 ** (b + 1), 2 ** (L - b - 1), chi) for b in range(L - 1)]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=21, dims=dims)
+    runs = []
+    for n in (1, 16):
+        with lt.Ensemble(L, chi, n, precision=lt.LT_MIXED, dt=0.02, gamma_loss=0.2,
+                         svd_cut=1e-6) as e:
+            e.set_state(0, [(B, lam, dims)] * n)
+            e.apply_layer(0, 0.02)
+            e.apply_layer(1, 0.02)
+            runs.append((e.get_state(0, 1), lt.lt_cluster_launches(e.ctx)))
+    (d1, l1, b1), c1 = runs[0]
+    (d2, l2, b2), c2 = runs[1]
+    assert c1 == 2 and c2 == 0
+    assert np.array_equal(d1, d2)
+    assert np.array_equal(l1, l2)
+    assert np.array_equal(b1, b2)
