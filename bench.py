@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--qsd-steps", type=int, default=2)
     ap.add_argument("--qsd-chi128-traj", type=int, default=64)
     ap.add_argument("--qsd-full-traj", type=int, default=1024)
-    ap.add_argument("--qsd-cap-s", type=float, default=30.0)
+    ap.add_argument("--qsd-cap-s", type=float, default=75.0)
+    ap.add_argument("--qsd-acc-hist", type=int, default=16)
     ap.add_argument("--mpdo-steps", type=int, default=250)
     ap.add_argument("--mpdo-sat-steps", type=int, default=2)
     ap.add_argument("--dm-cap-s", type=float, default=45.0)
@@ -817,6 +818,27 @@ def run_ours(args):
                     "final_mean_bond_dim": float(dimsf.mean()),
                     "log_weight_range": [float(lwf.min()), float(lwf.max())]}
                 ef.close()
+                # accuracy: a few histories of the same run in both precisions (the noise is
+                # the same Philox draws, so they differ by rounding only), to T = 2
+                if args.qsd_acc_hist > 0:
+                    res = {}
+                    for pname, prec in (("mixed", lt.LT_MIXED), ("fp64", lt.LT_FP64)):
+                        ea = reg(lt.Ensemble(Lq, 128, args.qsd_acc_hist, method=lt.LT_QSD,
+                                             precision=prec, init="neel", dt=dtq,
+                                             gamma_loss=0.05, gamma_deph=0.1, fermionic_jumps=0,
+                                             svd_cut=1e-6, stream=stream.cuda_stream))
+                        lt.lt_step(ea.ctx, 200)
+                        mean_a, _, per_a = ea.density(per_traj=True)
+                        res[pname] = (mean_a, per_a, ea.log_weights())
+                        ea.close()
+                    (m1, p1, w1), (m2, p2, w2) = res["mixed"], res["fp64"]
+                    qsd["config_T2"]["mixed_vs_fp64_T2"] = {
+                        "histories": args.qsd_acc_hist, "steps": 200,
+                        "max_abs_density_weighted_estimator": float(np.abs(m1 - m2).max()),
+                        "max_abs_density_per_history": float(np.abs(p1 - p2).max()),
+                        "max_abs_log_weight": float(np.abs(w1 - w2).max()),
+                        "how": "same histories (same Philox noise) in both precisions, the same "
+                               "svd_cut 1e-6"}
     except Exception as err:  # recorded in the line; the headline still prints
         qsd = failed(err)
     finally:

@@ -289,7 +289,16 @@ cudaError_t launch_convert_in(lt_ctx_s* c, const double* src, long long n, long 
 cudaError_t launch_convert_out(lt_ctx_s* c, double* dst, long long n, long long src_off);
 cudaError_t launch_init_state(lt_ctx_s* c, const uint8_t* occ_dev);
 size_t bond_smem_bytes(int chi, size_t celt, int d);
-#define LT_CL_STATE (LT_MAX_DIM + 8)  // floats of shared Jacobi state per cluster
+// Per-cluster state of the cluster-shared phases, in floats (global memory):
+#define LT_CL_NRM 0                        // Jacobi row norms [LT_MAX_DIM]
+#define LT_CL_FLG LT_MAX_DIM               // Jacobi flags and rotation count (8 ints)
+#define LT_CL_B1 (LT_MAX_DIM + 8)          // betas of the LQ of theta [LT_MAX_DIM]
+#define LT_CL_B2 (2 * LT_MAX_DIM + 8)      // betas of the LQ of L1^+, two in turn
+#define LT_CL_E2 (2 * LT_MAX_DIM + 16)     // its reflectors, two of LT_MAX_DIM complex
+#define LT_CL_PERM (6 * LT_MAX_DIM + 16)   // ranked rows [LT_MAX_DIM] (ints)
+#define LT_CL_SIG (7 * LT_MAX_DIM + 16)    // squared singular values [LT_MAX_DIM] (doubles)
+#define LT_CL_K (9 * LT_MAX_DIM + 16)      // kept values (int)
+#define LT_CL_STATE (9 * LT_MAX_DIM + 32)
 size_t env_scratch_elems(int L, int chi);
 #define LT_ENV_SCRATCH_BYTES (4ull << 30)  // cap of the environment kernels' scratch
 long long env_grid_cap(int L, int chi, size_t celt, int num_sms);

@@ -842,24 +842,26 @@ __device__ __forceinline__ void unit_phase(R xr, R xi, R& phr, R& phi, R& ax) {
   ax = m * nn;
 }
 
-template <typename R>
+template <typename R, bool CG = false>
 __device__ __forceinline__ R make_reflector(R* Xr, R* Xi, int base, int st, int len,
                                             typename CT<R>::T* dst) {
   typedef typename CT<R>::T Tc;
+  // CG: the entries may have been written by another CTA of the cluster; read past L1
+  auto ld = [](const R* p) { return CG ? __ldcg(p) : *p; };
   const int lane = threadIdx.x & 31;
   R a2 = 0, dummy = 0;
   for (int t = lane; t < len; t += 32) {
-    const R u = Xr[base + t * st], w = Xi[base + t * st];
+    const R u = ld(Xr + base + t * st), w = ld(Xi + base + t * st);
     a2 = fma(u, u, fma(w, w, a2));
   }
   warp_sum2(a2, dummy);
-  const R x0r = Xr[base], x0i = Xi[base];
+  const R x0r = ld(Xr + base), x0i = ld(Xi + base);
   const R alpha = sqrt(a2);
   const bool tiny = !(alpha > TinyNorm<R>::v);
   R phr, phi, ax0;
   unit_phase(x0r, x0i, phr, phi, ax0);
   for (int t = lane; t < len; t += 32) {
-    Tc e = cmk<Tc>(Xr[base + t * st], Xi[base + t * st]);
+    Tc e = cmk<Tc>(ld(Xr + base + t * st), ld(Xi + base + t * st));
     if (t == 0) {
       e.x += phr * alpha;
       e.y += phi * alpha;
@@ -911,6 +913,119 @@ __device__ __forceinline__ void lq_update_warp(R* Xr, R* Xi, int ldp, int m, int
       }
     }
   }
+}
+
+// In-place conjugate transpose of the leading m x m block of the planar matrix
+// (barriers before and after); CG: read past L1 (other CTAs of a cluster wrote it).
+template <typename R, bool CG = false>
+__device__ void conj_transpose_square(R* Xr, R* Xi, int ldp, int m) {
+  auto ld = [](const R* p) { return CG ? __ldcg(p) : *p; };
+  __syncthreads();
+  const int np = m * (m + 1) / 2;  // entries on and above the diagonal
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    // row i, column j >= i of the upper triangle, t enumerating rows of m - i entries
+    int i = (int)((2.0 * m + 1.0 - sqrt((2.0 * m + 1.0) * (2.0 * m + 1.0) - 8.0 * t)) / 2.0);
+    while (i > 0 && (long long)i * (2 * m - i + 1) / 2 > t) --i;
+    while ((long long)(i + 1) * (2 * m - i) / 2 <= t) ++i;
+    const int j = i + (t - i * (2 * m - i + 1) / 2);
+    const long long a = (long long)i * ldp + j, b = (long long)j * ldp + i;
+    const R ar = ld(Xr + a), ai = ld(Xi + a), br = ld(Xr + b), bi = ld(Xi + b);
+    Xr[a] = br;
+    Xi[a] = -bi;
+    Xr[b] = ar;
+    Xi[b] = -ai;
+  }
+  __syncthreads();
+}
+
+// An LQ (rows 0..m-1 of n columns, r reflectors) shared by the C CTAs of a cluster, the
+// same arithmetic as qr_precondition's warp-per-row steps: row i belongs to warp
+// i mod (C nw) of the cluster (warp w of rank c is number c nw + w), whose lanes hold its
+// columns l + 32 u; the owner of row j builds reflector j into E (packed at the offset
+// sum_{t<j} (n - t), or into two buffers in turn) and its beta into gb (gb[j], or the
+// two in turn); one cluster barrier per step, and one at the end.  Rows and reflectors
+// are read past L1: other CTAs write them.
+template <int EPL>
+__device__ void lq_cluster(float* Xr, float* Xi, int ldp, int m, int n, int r, float2* E,
+                           bool packed, float* gb, int crank, int C) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int GW = C * nw, gw = crank * nw + warp;
+  long long off = 0;
+  for (int j = 0; j < r; ++j) {
+    const int len = n - j;
+    float2* e = packed ? E + off : E + (j & 1) * LT_MAX_DIM;
+    float* bp = packed ? gb + j : gb + (j & 1);
+    if (j % GW == gw) {
+      const float bt = make_reflector<float, true>(Xr, Xi, j * ldp + j, 1, len, e);
+      if (lane == 0) *bp = bt;
+    }
+    __threadfence();
+    cluster_sync();
+    const float bt = __ldcg(bp);
+    // this warp's first row after j
+    const int i0 = j + 1 + (((gw - (j + 1)) % GW) + GW) % GW;
+    if (bt != 0.f && i0 < m) {
+      float2 ev[EPL];
+#pragma unroll
+      for (int u = 0; u < EPL; ++u) {
+        const int c = lane + 32 * u;
+        ev[u] = c < len ? __ldcg(e + c) : make_float2(0.f, 0.f);
+      }
+      for (int i = i0; i < m; i += GW) {
+        float* __restrict__ xr = Xr + (long long)i * ldp + j;
+        float* __restrict__ xi = Xi + (long long)i * ldp + j;
+        float a[EPL], b[EPL];
+        float dr = 0.f, di = 0.f;  // d = sum_c x_c conj(e_c)
+#pragma unroll
+        for (int u = 0; u < EPL; ++u) {
+          const int c = lane + 32 * u;
+          a[u] = c < len ? __ldcg(xr + c) : 0.f;
+          b[u] = c < len ? __ldcg(xi + c) : 0.f;
+          dr = fmaf(a[u], ev[u].x, fmaf(b[u], ev[u].y, dr));
+          di = fmaf(b[u], ev[u].x, fmaf(-a[u], ev[u].y, di));
+        }
+        warp_sum2(dr, di);
+        dr *= bt;
+        di *= bt;
+#pragma unroll
+        for (int u = 0; u < EPL; ++u) {  // x -= beta d e
+          const int c = lane + 32 * u;
+          if (c < len) {
+            xr[c] = a[u] - fmaf(dr, ev[u].x, -di * ev[u].y);
+            xi[c] = b[u] - fmaf(dr, ev[u].y, di * ev[u].x);
+          }
+        }
+      }
+    }
+    off += len;
+  }
+  __threadfence();
+  cluster_sync();
+}
+
+// The two-level preconditioning of a task with m <= n and m > 128, shared by the C CTAs
+// of a cluster (the same factors as qr_precondition): the LQ of theta with its reflectors
+// packed into Vst and its betas in the cluster state, then the QR of the square L1 as
+// the LQ of L1^+ (rank 0 transposes before and after).  Starts with a cluster barrier
+// (rank 0's theta visible); every CTA takes the same barriers.
+__device__ __noinline__ void precondition_cluster(float* Xr, float* Xi, int ldp, int m, int n,
+                                                  float2* Vst, float* cl_state, int crank,
+                                                  int C) {
+  __threadfence();
+  cluster_sync();
+  if (n > 256)
+    lq_cluster<16>(Xr, Xi, ldp, m, n, m, Vst, true, cl_state + LT_CL_B1, crank, C);
+  else
+    lq_cluster<8>(Xr, Xi, ldp, m, n, m, Vst, true, cl_state + LT_CL_B1, crank, C);
+  if (crank == 0) conj_transpose_square<float, true>(Xr, Xi, ldp, m);
+  __threadfence();
+  cluster_sync();
+  float2* E2 = reinterpret_cast<float2*>(cl_state + LT_CL_E2);
+  if (m > 256)
+    lq_cluster<16>(Xr, Xi, ldp, m, m, m, E2, false, cl_state + LT_CL_B2, crank, C);
+  else
+    lq_cluster<8>(Xr, Xi, ldp, m, m, m, E2, false, cl_state + LT_CL_B2, crank, C);
+  if (crank == 0) conj_transpose_square<float, true>(Xr, Xi, ldp, m);
 }
 
 template <typename R>
@@ -982,6 +1097,30 @@ __device__ void qr_precondition(R* Xr, R* Xi, int ldp, int m, int n, int r,
     }
     __syncthreads();
     off += len;
+  }
+  if (r == m && m > 128) {
+    // square L1 wider than 128: its QR as the LQ of L1^+ (if L1^+ = L' Q^+ then
+    // L1 = Q L'^+, so R2 = L'^+ with the same diagonal phases), which takes the
+    // coalesced warp-per-row steps; the reflectors go through su, Q is discarded
+    conj_transpose_square(Xr, Xi, ldp, m);
+    for (int j = 0; j < m; ++j) {
+      const int len = m - j;
+      if (warp == 0) {
+        const R bt = make_reflector<R>(Xr, Xi, j * ldp + j, 1, len, su);
+        if ((threadIdx.x & 31) == 0) beta[LT_MAX_DIM] = bt;
+      }
+      __syncthreads();
+      const R bt = beta[LT_MAX_DIM];
+      if (bt != (R)0) {
+        if (m > 256)
+          lq_update_warp<R, 16>(Xr, Xi, ldp, m, j, len, su, bt);
+        else
+          lq_update_warp<R, 8>(Xr, Xi, ldp, m, j, len, su, bt);
+      }
+      __syncthreads();
+    }
+    conj_transpose_square(Xr, Xi, ldp, m);
+    return;
   }
   // QR of the lower-trapezoidal L1 (columns 0..r-1): reflectors from the columns,
   // applied from the left to the columns on their right, one thread per column;
@@ -1370,6 +1509,147 @@ __device__ void apply_q1(R* Xr, R* Xi, int ldp, int n, int r, int k, const int* 
 // G s + q (s < 128 / G) as float2 pairs (2 G h + q, 2 G h + G + q); the
 // reflectors are read from their packed store with no barrier between them, and
 // Y (which overlays that store) is written after one barrier at the end.
+// V_k^+ for rows longer than 128 columns (single precision): a warp takes one of the k
+// kept rows at a time and keeps it in registers (lane l the columns l + 32 u) through all
+// r reflectors, which it reads coalesced; each inner product is summed over the warp.
+// The same result as apply_q1 up to the order of the sums.  Rows are written back in
+// place; the caller copies them into V_k^+'s region (which holds the reflectors until
+// every row is done).  The k rows are dealt over the warps of `parts` CTAs (a cluster's),
+// this CTA taking share `part`.
+template <int EPL, bool CG = false>
+__device__ void apply_q1_wide(float* Xr, float* Xi, int ldp, int n, int r, int k, const int* perm,
+                              const double* sig, const float2* Vst, const float* beta, int part,
+                              int parts) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int total = r * n - r * (r - 1) / 2;
+  auto ld = [](const float* q) { return CG ? __ldcg(q) : *q; };
+  for (int j = part * nw + warp; j < k; j += parts * nw) {
+    const int p = CG ? __ldcg(perm + j) : perm[j];
+    const double sg = CG ? __ldcg(sig + p) : sig[p];
+    const float inv = sg > 0.0 ? (float)(1.0 / sqrt(sg)) : 0.f;
+    float* xr = Xr + (long long)p * ldp;
+    float* xi = Xi + (long long)p * ldp;
+    float ar[EPL], ai[EPL];
+#pragma unroll
+    for (int u = 0; u < EPL; ++u) {
+      const int c = lane + 32 * u;
+      ar[u] = c < n ? ld(xr + c) * inv : 0.f;
+      ai[u] = c < n ? ld(xi + c) * inv : 0.f;
+    }
+    int off = total;
+    for (int l = r - 1; l >= 0; --l) {
+      off -= n - l;
+      const float bt = ld(beta + l);
+      if (bt == 0.f) continue;
+      const float2* e = Vst + off - l;  // e[c] for columns c >= l
+      float dr = 0.f, di = 0.f;       // d = sum_c x_c conj(e_c)
+      float2 w[EPL];
+#pragma unroll
+      for (int u = 0; u < EPL; ++u) {
+        const int c = lane + 32 * u;
+        w[u] = c >= l && c < n ? (CG ? __ldcg(e + c) : e[c]) : make_float2(0.f, 0.f);
+        dr = fmaf(ar[u], w[u].x, fmaf(ai[u], w[u].y, dr));
+        di = fmaf(ai[u], w[u].x, fmaf(-ar[u], w[u].y, di));
+      }
+      warp_sum2(dr, di);
+      dr *= bt;
+      di *= bt;
+#pragma unroll
+      for (int u = 0; u < EPL; ++u) {  // x -= beta d e
+        ar[u] -= fmaf(dr, w[u].x, -di * w[u].y);
+        ai[u] -= fmaf(dr, w[u].y, di * w[u].x);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EPL; ++u) {
+      const int c = lane + 32 * u;
+      if (c < n) {
+        xr[c] = ar[u];
+        xi[c] = ai[u];
+      }
+    }
+  }
+}
+
+// The generic preconditioning and V_k^+ of the single-precision kernel, kept out of line
+// so that they do not take registers from its register paths.
+__device__ __noinline__ void qr_precondition_f(float* Xr, float* Xi, int ldp, int m, int n, int r,
+                                               float2* Vst, float* beta, float2* su) {
+  qr_precondition<float>(Xr, Xi, ldp, m, n, r, Vst, beta, su);
+}
+__device__ __noinline__ void apply_q1_f(float* Xr, float* Xi, int ldp, int n, int r, int k,
+                                        const int* perm, const double* sig, const float2* Vst,
+                                        const float* beta, float2* Y, int ldy) {
+  apply_q1<float>(Xr, Xi, ldp, n, r, k, perm, sig, Vst, beta, Y, ldy);
+}
+
+// V_k^+ of a task with rows longer than 128 columns, by one CTA: the rows in place, then
+// (every reflector read) copied into V_k^+'s region Y.
+__device__ __noinline__ void wide_q1(float* Xr, float* Xi, int ldp, int n, int r, int k,
+                                     const int* perm, const double* sig, float2* Y,
+                                     const float* beta, int ldy) {
+  __syncthreads();
+  if (n > 256)
+    apply_q1_wide<16>(Xr, Xi, ldp, n, r, k, perm, sig, Y, beta, 0, 1);
+  else
+    apply_q1_wide<8>(Xr, Xi, ldp, n, r, k, perm, sig, Y, beta, 0, 1);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * n; idx += blockDim.x) {
+    const int j = idx / n, c = idx - j * n;
+    const long long o = (long long)perm[j] * ldp + c;
+    Y[j * ldy + c] = make_float2(Xr[o], Xi[o]);
+  }
+}
+
+// Whether a cluster also shares the preconditioning and V_k^+ of a task whose Jacobi it
+// shares: theta no taller than wide (m <= n), so that L1 is square, and wider than 128.
+__device__ __forceinline__ bool cluster_shares_precondition(int m, int n) {
+  return m <= n && m > LT_REG_DIM;
+}
+
+// V_k^+ shared by a cluster: rank 0 publishes k, the ranked rows and the squared singular
+// values (cluster_q1_lead), every CTA transforms its share of the k rows in place
+// (reflectors and betas from the cluster's LQ), and rank 0 copies them into V_k^+'s
+// region once all are done.  Two cluster barriers, taken by every CTA.
+__device__ void cluster_q1_rows(float* Xr, float* Xi, int ldp, int n, int r, const float2* Vst,
+                                const float* cls, int crank, int C) {
+  __threadfence();
+  cluster_sync();  // k, ranks and singular values published
+  const int k = __ldcg(reinterpret_cast<const int*>(cls + LT_CL_K));
+  const int* perm = reinterpret_cast<const int*>(cls + LT_CL_PERM);
+  const double* sig = reinterpret_cast<const double*>(cls + LT_CL_SIG);
+  if (n > 256)
+    apply_q1_wide<16, true>(Xr, Xi, ldp, n, r, k, perm, sig, Vst, cls + LT_CL_B1, crank, C);
+  else
+    apply_q1_wide<8, true>(Xr, Xi, ldp, n, r, k, perm, sig, Vst, cls + LT_CL_B1, crank, C);
+  __threadfence();
+  cluster_sync();  // every row transformed
+}
+
+__device__ __noinline__ void cluster_q1(float* Xr, float* Xi, int ldp, int n, int r,
+                                        const float2* Vst, float* cls, int crank, int C) {
+  cluster_q1_rows(Xr, Xi, ldp, n, r, Vst, cls, crank, C);
+}
+
+__device__ __noinline__ void cluster_q1_lead(float* Xr, float* Xi, int ldp, int n, int r, int k,
+                                             const int* perm, const double* sig, float2* Y,
+                                             int ldy, float* cls, int C) {
+  int* gperm = reinterpret_cast<int*>(cls + LT_CL_PERM);
+  double* gsig = reinterpret_cast<double*>(cls + LT_CL_SIG);
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    gperm[i] = perm[i];
+    gsig[i] = sig[i];
+  }
+  if (threadIdx.x == 0) *reinterpret_cast<int*>(cls + LT_CL_K) = k;
+  __syncthreads();
+  cluster_q1_rows(Xr, Xi, ldp, n, r, Y, cls, 0, C);
+  for (int idx = threadIdx.x; idx < k * n; idx += blockDim.x) {
+    const int j = idx / n, c = idx - j * n;
+    const long long o = (long long)perm[j] * ldp + c;
+    Y[j * ldy + c] = make_float2(__ldcg(Xr + o), __ldcg(Xi + o));
+  }
+}
+
 template <int G>
 __device__ void apply_q1_reg(const float* Xr, const float* Xi, int ldp, int n, int r, int k,
                              const int* perm, const double* sig, const float2* Vst,
@@ -2055,8 +2335,15 @@ __device__ __noinline__ void cluster_helper(const BondArgs<float>& a, float* s_n
       continue;
     if (in_smem || !lay.wide2) continue;
     float* W = reinterpret_cast<float*>(a.scratch + cid * C * a.scratch_stride);
-    wide_jacobi(W, W + (long long)lay.mcap * lay.ldp, lay.ldp, lay.mp2, lay.rr, lay.npad2, s_nrm,
-                s_part, s_nrot, a.max_sweeps, a.tol, C, crank, a.cl_state + cid * LT_CL_STATE);
+    float* Xr = W;
+    float* Xi = W + (long long)lay.mcap * lay.ldp;
+    float2* Y = reinterpret_cast<float2*>(W + 2ll * lay.mcap * lay.ldp);
+    float* cls = a.cl_state + cid * LT_CL_STATE;
+    const bool cl_pre = cluster_shares_precondition(lay.mJ, lay.nJ);
+    if (cl_pre) precondition_cluster(Xr, Xi, lay.ldp, lay.mJ, lay.nJ, Y, cls, crank, C);
+    wide_jacobi(Xr, Xi, lay.ldp, lay.mp2, lay.rr, lay.npad2, s_nrm, s_part, s_nrot, a.max_sweeps,
+                a.tol, C, crank, cls);
+    if (cl_pre) cluster_q1(Xr, Xi, lay.ldp, lay.nJ, lay.rr, Y, cls, crank, C);
   }
 }
 
@@ -2173,8 +2460,14 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
         qr_precondition_reg<BondShape<R>::NT / LT_REG_DIM>(
             reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ, rr, mp2, npad2,
             reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta));
+      else if (shared_jac && cluster_shares_precondition(mJ, nJ))
+        precondition_cluster(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ,
+                             nJ, reinterpret_cast<float2*>(Y), a.cl_state + cid * LT_CL_STATE, 0,
+                             C);
       else
-        qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
+        qr_precondition_f(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, mJ, nJ,
+                          rr, reinterpret_cast<float2*>(Y), reinterpret_cast<float*>(s_beta),
+                          reinterpret_cast<float2*>(s_u));
     } else {
       qr_precondition<R>(Xr, Xi, ldp, mJ, nJ, rr, Y, s_beta, s_u);
     }
@@ -2299,8 +2592,17 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
             reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi), ldp, nJ, rr, k,
             s_perm, s_sig, reinterpret_cast<const float2*>(Y), reinterpret_cast<const float*>(s_beta),
             reinterpret_cast<float2*>(Y), ld);
+      else if (shared_jac && cluster_shares_precondition(mJ, nJ))
+        cluster_q1_lead(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, nJ, rr, k,
+                        s_perm, s_sig, reinterpret_cast<float2*>(Y), ld,
+                        a.cl_state + cid * LT_CL_STATE, C);
+      else if (nJ > LT_REG_DIM)
+        wide_q1(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, nJ, rr, k, s_perm,
+                s_sig, reinterpret_cast<float2*>(Y), reinterpret_cast<const float*>(s_beta), ld);
       else
-        apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
+        apply_q1_f(reinterpret_cast<float*>(Xr), reinterpret_cast<float*>(Xi), ldp, nJ, rr, k,
+                   s_perm, s_sig, reinterpret_cast<const float2*>(Y),
+                   reinterpret_cast<const float*>(s_beta), reinterpret_cast<float2*>(Y), ld);
     } else {
       apply_q1<R>(Xr, Xi, ldp, nJ, rr, k, s_perm, s_sig, Y, s_beta, Y, ld);
     }
@@ -3942,9 +4244,10 @@ cudaError_t configure_bond(lt_ctx_s* c) {
     el = c->prec == LT_MIXED ? bond_smem_limit<float, 2>(c->device, &limit)
                              : bond_smem_limit<double, 2>(c->device, &limit);
   if (el != cudaSuccess) return el;
-  // every launch gets shared memory for the tasks that fit it; global scratch is
-  // added for the larger ones when the largest task does not fit
-  c->bond_smem = need <= limit ? need : limit;
+  // every launch gets shared memory for the tasks that fit it, and global scratch for the
+  // larger ones when the largest task does not fit; except in double precision, whose
+  // tasks at such sizes nearly all work in scratch and run faster with the whole L1
+  c->bond_smem = need <= limit ? need : (c->prec == LT_MIXED ? limit : 0);
   cudaError_t e;
   int occ = 0;
   // The dynamic shared-memory ceiling is a property of the kernel, shared by
