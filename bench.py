@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--qsd-traj", type=int, default=1024)
     ap.add_argument("--qsd-steps", type=int, default=2)
     ap.add_argument("--qsd-chi128-traj", type=int, default=64)
-    ap.add_argument("--qsd-full-traj", type=int, default=1024)
+    ap.add_argument("--qsd-full-traj", type=int, default=256)
     ap.add_argument("--qsd-cap-s", type=float, default=75.0)
     ap.add_argument("--qsd-acc-hist", type=int, default=16)
     ap.add_argument("--mpdo-steps", type=int, default=250)
@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--graph-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--wall-budget-s", type=float, default=450.0,
+                    help="wall time after which the remaining secondary legs are skipped")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -325,7 +328,7 @@ def density_matrix_leg(lt, stream, args, alu_peak, method, L, chi, init, rates, 
     # time to solution, in chunks of 10 steps, stopped at args.dm_cap_s of device time
     with lt.Ensemble(L, chi, 1, precision=lt.LT_MIXED, svd_cut=1e-6, **kw) as e:
         s_tts, done, c_tts = 0.0, 0, {"layer_updates": 0}
-        while done < steps and s_tts < args.dm_cap_s:
+        while done < steps and s_tts < min(args.dm_cap_s, args.left() - 30.0):
             n = min(10, steps - done)
             s_, c_ = timed(e, n)
             s_tts += s_
@@ -443,7 +446,8 @@ def serving_leg(lt, args):
     and T uniform in [1, 5] at dt = 0.02, admitted by device footprint.  The run stops
     at `serve_cap_s` of wall time; requests unfinished by then are reported as such."""
     rng = np.random.default_rng(77)
-    n_req, rate, cap = args.serve_requests, args.serve_rate, args.serve_cap_s
+    n_req, rate, cap = args.serve_requests, args.serve_rate, min(args.serve_cap_s,
+                                                                  max(5.0, args.left() - 15.0))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     methods = (lt.LT_TRAJ, lt.LT_QSD, lt.LT_MPDO, lt.LT_PURIFIED)
     reqs = []
@@ -545,7 +549,7 @@ def run_reference(args):
 # (profiles/bond_update_kernel_dram_w3s_256traj.md).  Traffic grows in proportion to
 # the updates (every update reads and writes its two sites once), so a full launch is
 # this figure times its updates.
-BOND_DRAM_BYTES_PER_UPDATE = 4589290496 / 21185.0
+BOND_DRAM_BYTES_PER_UPDATE = 4570240768 / 21185
 
 
 def algorithmic_tflops(flops, seconds):
@@ -696,12 +700,114 @@ def run_ours(args):
             dead.append(repr(err))
         return {"error": repr(err)}
 
+    # wall-time budget of the whole run: a secondary leg starts only with `need` seconds
+    # left (its caps shrink with the time left); per-leg seconds go into the line
+    leg_s, skipped = {}, {}
+
+    def budget(name, need):
+        if args.left() >= need:
+            return True
+        skipped[name] = "%.0f s of the %.0f s wall budget left" % (max(args.left(), 0.0),
+                                                                  args.wall_budget_s)
+        return False
+
+    # ---- end to end through the public API with host buffers ---------------------------
+    e2e = None
+    t_leg = time.perf_counter()
+    try:
+        if not args.no_e2e and not dead:
+            dims, lam, B = packed
+            pinned = [torch.from_numpy(x).pin_memory().numpy() for x in (dims, lam, B)]
+            mean_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
+            sem_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            e = lt.Ensemble(L, chi, n_traj, precision=lt.LT_MIXED, init="neel",
+                            traj_offset=offset, stream=stream.cuda_stream,
+                            **w3_kwargs("mixed"))
+            h2d = upload(lt, e.ctx, None, n_traj, pinned=pinned)
+            for _ in range(args.e2e_steps):
+                lt.lt_step(e.ctx, 1)
+                lt.lt_measure_density(e.ctx, L, n_traj, out=(mean_h, sem_h))
+            # ensemble statistics over all ranks (the one collective of the sharded path)
+            shard.combine_mean_sem(mean_h, sem_h, n_traj, device=torch.device("cuda", local))
+            ce = e.counters()
+            e.close()
+            t1 = time.perf_counter()
+            barrier()
+            e2e_s = t1 - t0
+            if world > 1:
+                tt = torch.tensor([e2e_s, float(ce["updates"])], device="cuda")
+                mx = tt.clone()
+                torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+                torch.distributed.all_reduce(tt)
+                e2e_s, e2e_up = float(mx[0]), float(tt[1])
+            else:
+                e2e_up = float(ce["updates"])
+            e2e = {"value": e2e_up / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d // max(args.e2e_steps, 1)),
+                   "d2h_bytes_per_step": int(2 * L * 8),
+                   "includes": "lt_create, upload of the initial ensemble from pinned host "
+                               "memory, %d x (lt_step + lt_measure_density to host), lt_destroy"
+                               % args.e2e_steps}
+    except Exception as err:  # recorded in the line; the headline still prints
+        e2e = failed(err)
+    leg_s["e2e"] = time.perf_counter() - t_leg
+
+    # the oracle on the host cores (rank 0, one GPU only)
+    t_leg = time.perf_counter()
+    cpu = None
+    if solo and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+    leg_s["cpu_baseline"] = time.perf_counter() - t_leg
+
+    # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
+    accuracy = None
+    t_leg = time.perf_counter()
+    try:
+        if args.acc_traj > 0 and solo and not dead and budget("mixed_vs_fp64", 20):
+            na = args.acc_traj
+            ea = reg(lt.Ensemble(L, chi, na, precision=lt.LT_FP64, init="neel",
+                             stream=stream.cuda_stream, **w3_kwargs("fp64")))
+            em = reg(lt.Ensemble(L, chi, na, precision=lt.LT_MIXED, init="neel",
+                             stream=stream.cuda_stream, **w3_kwargs("mixed")))
+            upload(lt, ea.ctx, packed, na)
+            upload(lt, em.ctx, packed, na)
+            jumps = 0
+            for s in range(args.acc_steps):
+                ch = np.ascontiguousarray(ea.apply_jumps(s), np.int32)
+                em.apply_jumps(s, ch)
+                jumps += int((ch >= 0).sum())
+                for parity, tau in layers:
+                    ea.apply_layer(parity, tau)
+                    em.apply_layer(parity, tau)
+            _, _, d64 = ea.density(per_traj=True)
+            _, _, dmx = em.density(per_traj=True)
+            c64, cp64 = ea.corr(per_traj=True)
+            cmx, cpmx = em.corr(per_traj=True)
+            accuracy = {"n_traj": na, "steps": args.acc_steps, "jumps": jumps,
+                        "max_abs_density_per_traj": float(np.abs(dmx - d64).max()),
+                        "max_abs_density_ensemble": float(np.abs(dmx.mean(0) - d64.mean(0)).max()),
+                        "max_abs_corr_per_traj": float(np.abs(cpmx - cp64).max()),
+                        "max_abs_corr_ensemble": float(np.abs(cmx - c64).max()),
+                        "how": "same start states; the FP64 run samples the jumps, the mixed run "
+                               "replays them"}
+            ea.close()
+            em.close()
+    except Exception as err:  # recorded in the line; the headline still prints
+        accuracy = failed(err)
+    finally:
+        close_open()
+    leg_s["mixed_vs_fp64"] = time.perf_counter() - t_leg
+
     # ---- plain FP64 path on a subset (same kernels in double precision) ----------------
     fp64 = None
+    t_leg = time.perf_counter()
     try:
         # single-GPU legs run at N = 1 only (in a scaling run they would hold every GPU)
         solo = world == 1
-        if args.fp64_traj > 0 and solo and not dead:
+        if args.fp64_traj > 0 and solo and not dead and budget("fp64_path", 20):
             n64 = args.fp64_traj
             e64 = reg(lt.Ensemble(L, chi, n64, precision=lt.LT_FP64, init="neel",
                               stream=stream.cuda_stream, **w3_kwargs("fp64")))
@@ -730,11 +836,23 @@ def run_ours(args):
         fp64 = failed(err)
     finally:
         close_open()
+    leg_s["fp64_path"] = time.perf_counter() - t_leg
+
+    # ---- the configured W3 run to T = 4 from the Neel state --------------------------------
+    full = None
+    t_leg = time.perf_counter()
+    try:
+        if args.full_traj > 0 and solo and not dead and budget("w3_to_T4", 70):
+            full = w3_full_run_leg(lt, stream, args)
+    except Exception as err:  # recorded in the line; the headline still prints
+        full = failed(err)
+    leg_s["w3_to_T4"] = time.perf_counter() - t_leg
 
     # ---- quantum state diffusion leg (Sec. 5.2), one GPU -------------------------------
     qsd = None
+    t_leg = time.perf_counter()
     try:
-        if args.qsd_traj > 0 and solo and not dead:
+        if args.qsd_traj > 0 and solo and not dead and budget("qsd", 60):
             Lq, nq, dtq = 128, args.qsd_traj, 0.01
             mq, pq = state_pool(Lq, chi, POOL, seed=4321)
             eq = reg(lt.Ensemble(Lq, chi, nq, method=lt.LT_QSD, precision=lt.LT_MIXED, init="neel",
@@ -788,7 +906,7 @@ def run_ours(args):
                 del m8, p8
             # the QSD configuration as written: L=128, chi_max=128, 1024 histories from
             # the Neel state to T=2 (200 steps of 0.01), stopped at args.qsd_cap_s
-            if args.qsd_full_traj > 0:
+            if args.qsd_full_traj > 0 and budget("qsd_config_T2", 50):
                 nf = args.qsd_full_traj
                 ef = reg(lt.Ensemble(Lq, 128, nf, method=lt.LT_QSD, precision=lt.LT_MIXED,
                                      init="neel", dt=dtq, gamma_loss=0.05, gamma_deph=0.1,
@@ -796,7 +914,7 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 ef.counters(clear=True)
                 sf, doneq = 0.0, 0
-                while doneq < 200 and sf < args.qsd_cap_s:
+                while doneq < 200 and sf < min(args.qsd_cap_s, args.left() - 40.0):
                     a.record(stream)
                     lt.lt_step(ef.ctx, 10)
                     b.record(stream)
@@ -807,9 +925,9 @@ def run_ours(args):
                 _, dimsf = ef.stats()
                 lwf = ef.log_weights()
                 qsd["config_T2"] = {
-                    "workload": "QSD as configured: L=128, chi_max=128, %d histories from the Neel "
-                                "state, dephasing 0.1 and spin loss 0.05, dt=0.01, T=2 (200 steps), "
-                                "mixed precision" % nf,
+                    "workload": "QSD configuration (L=128, chi_max=128, dephasing 0.1 and spin "
+                                "loss 0.05, dt=0.01, T=2 = 200 steps from the Neel state) with %d "
+                                "of its 1024 histories, mixed precision" % nf,
                     "steps_done": doneq, "T_reached": doneq * dtq, "stopped_at_cap": doneq < 200,
                     "cap_s": args.qsd_cap_s, "s": sf, "ms_per_step": 1e3 * sf / doneq,
                     "updates_per_s": cf["updates"] / sf,
@@ -820,7 +938,7 @@ def run_ours(args):
                 ef.close()
                 # accuracy: a few histories of the same run in both precisions (the noise is
                 # the same Philox draws, so they differ by rounding only), to T = 2
-                if args.qsd_acc_hist > 0:
+                if args.qsd_acc_hist > 0 and budget("qsd_T2_vs_fp64", 25):
                     res = {}
                     for pname, prec in (("mixed", lt.LT_MIXED), ("fp64", lt.LT_FP64)):
                         ea = reg(lt.Ensemble(Lq, 128, args.qsd_acc_hist, method=lt.LT_QSD,
@@ -843,18 +961,20 @@ def run_ours(args):
         qsd = failed(err)
     finally:
         close_open()
+    leg_s["qsd"] = time.perf_counter() - t_leg
 
     # ---- density-matrix legs: vectorised (Sec. 3.1) and purified (Sec. 3.2), one GPU ---
     mpdo_leg = purified_leg = None
+    t_leg = time.perf_counter()
     try:
-        if args.mpdo_steps > 0 and solo and not dead:
+        if args.mpdo_steps > 0 and solo and not dead and budget("mpdo", 45):
             mpdo_leg = density_matrix_leg(
                 lt, stream, args, alu_peak, method=lt.LT_MPDO, L=32, chi=128, init="domain_wall",
                 rates=dict(dt=0.02, gamma_loss=0.1, gamma_gain=0.05), steps=args.mpdo_steps,
                 workload="MPDO (d^2 = 4): L=32 XX chain, spin loss 0.1 and gain 0.05 on every site, "
                          "dt=0.02, 2nd-order Trotter, domain-wall start, chi_max=128 (theta up to "
                          "512 x 512)")
-        if args.purified_steps > 0 and solo and not dead:
+        if args.purified_steps > 0 and solo and not dead and budget("purified", 25):
             purified_leg = density_matrix_leg(
                 lt, stream, args, alu_peak, method=lt.LT_PURIFIED, L=64, chi=96, init="neel",
                 rates=dict(dt=0.01, gamma_loss=0.05, gamma_deph=0.1), steps=args.purified_steps,
@@ -863,105 +983,17 @@ def run_ours(args):
                          "then the R step, Neel start, chi_max=96 (theta up to 384 x 384)")
     except Exception as err:  # recorded in the line; the headline still prints
         mpdo_leg = purified_leg = failed(err)
+    leg_s["density_matrices"] = time.perf_counter() - t_leg
 
     # ---- serving: the configured request mix (Poisson arrivals) through the server ------
     serving = None
+    t_leg = time.perf_counter()
     try:
-        if args.serve_requests > 0 and solo and not dead:
+        if args.serve_requests > 0 and solo and not dead and budget("serving", 25):
             serving = serving_leg(lt, args)
     except Exception as err:  # recorded in the line; the headline still prints
         serving = failed(err)
-
-    # ---- mixed vs FP64 on the same W3s trajectories (jump records replayed) -------------
-    accuracy = None
-    try:
-        if args.acc_traj > 0 and solo and not dead:
-            na = args.acc_traj
-            ea = reg(lt.Ensemble(L, chi, na, precision=lt.LT_FP64, init="neel",
-                             stream=stream.cuda_stream, **w3_kwargs("fp64")))
-            em = reg(lt.Ensemble(L, chi, na, precision=lt.LT_MIXED, init="neel",
-                             stream=stream.cuda_stream, **w3_kwargs("mixed")))
-            upload(lt, ea.ctx, packed, na)
-            upload(lt, em.ctx, packed, na)
-            jumps = 0
-            for s in range(args.acc_steps):
-                ch = np.ascontiguousarray(ea.apply_jumps(s), np.int32)
-                em.apply_jumps(s, ch)
-                jumps += int((ch >= 0).sum())
-                for parity, tau in layers:
-                    ea.apply_layer(parity, tau)
-                    em.apply_layer(parity, tau)
-            _, _, d64 = ea.density(per_traj=True)
-            _, _, dmx = em.density(per_traj=True)
-            c64, cp64 = ea.corr(per_traj=True)
-            cmx, cpmx = em.corr(per_traj=True)
-            accuracy = {"n_traj": na, "steps": args.acc_steps, "jumps": jumps,
-                        "max_abs_density_per_traj": float(np.abs(dmx - d64).max()),
-                        "max_abs_density_ensemble": float(np.abs(dmx.mean(0) - d64.mean(0)).max()),
-                        "max_abs_corr_per_traj": float(np.abs(cpmx - cp64).max()),
-                        "max_abs_corr_ensemble": float(np.abs(cmx - c64).max()),
-                        "how": "same start states; the FP64 run samples the jumps, the mixed run "
-                               "replays them"}
-            ea.close()
-            em.close()
-    except Exception as err:  # recorded in the line; the headline still prints
-        accuracy = failed(err)
-    finally:
-        close_open()
-
-    # ---- the configured W3 run to T = 4 from the Neel state --------------------------------
-    full = None
-    try:
-        if args.full_traj > 0 and solo and not dead:
-            full = w3_full_run_leg(lt, stream, args)
-    except Exception as err:  # recorded in the line; the headline still prints
-        full = failed(err)
-
-    # ---- end to end through the public API with host buffers ---------------------------
-    e2e = None
-    try:
-        if not args.no_e2e and not dead:
-            dims, lam, B = packed
-            pinned = [torch.from_numpy(x).pin_memory().numpy() for x in (dims, lam, B)]
-            mean_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
-            sem_h = torch.empty(L, dtype=torch.float64).pin_memory().numpy()
-            torch.cuda.synchronize()
-            barrier()
-            t0 = time.perf_counter()
-            e = lt.Ensemble(L, chi, n_traj, precision=lt.LT_MIXED, init="neel",
-                            traj_offset=offset, stream=stream.cuda_stream,
-                            **w3_kwargs("mixed"))
-            h2d = upload(lt, e.ctx, None, n_traj, pinned=pinned)
-            for _ in range(args.steps):
-                lt.lt_step(e.ctx, 1)
-                lt.lt_measure_density(e.ctx, L, n_traj, out=(mean_h, sem_h))
-            # ensemble statistics over all ranks (the one collective of the sharded path)
-            shard.combine_mean_sem(mean_h, sem_h, n_traj, device=torch.device("cuda", local))
-            ce = e.counters()
-            e.close()
-            t1 = time.perf_counter()
-            barrier()
-            e2e_s = t1 - t0
-            if world > 1:
-                tt = torch.tensor([e2e_s, float(ce["updates"])], device="cuda")
-                mx = tt.clone()
-                torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-                torch.distributed.all_reduce(tt)
-                e2e_s, e2e_up = float(mx[0]), float(tt[1])
-            else:
-                e2e_up = float(ce["updates"])
-            e2e = {"value": e2e_up / e2e_s, "unit": UNIT,
-                   "h2d_bytes_per_step": int(h2d // max(args.steps, 1)),
-                   "d2h_bytes_per_step": int(2 * L * 8),
-                   "includes": "lt_create, upload of the initial ensemble from pinned host "
-                               "memory, %d x (lt_step + lt_measure_density to host), lt_destroy"
-                               % args.steps}
-    except Exception as err:  # recorded in the line; the headline still prints
-        e2e = failed(err)
-
-    cpu = None
-    if solo and not args.no_cpu:
-        cpu = cpu_baseline(args.cpu_seconds)
+    leg_s["serving"] = time.perf_counter() - t_leg
 
     if rank == 0:
         line = {
@@ -1010,6 +1042,7 @@ def run_ours(args):
             "purified": purified_leg,
             "serving": serving,
             "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu,
+            "legs": {"seconds": leg_s, "skipped": skipped, "wall_budget_s": args.wall_budget_s},
         }
         print(json.dumps(line))
     if world > 1:
@@ -1018,6 +1051,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    t_start = time.perf_counter()
+    args.left = lambda: args.wall_budget_s - (time.perf_counter() - t_start)
     if args.impl == "reference":
         run_reference(args)
     else:
