@@ -700,6 +700,9 @@ def run_ours(args):
             dead.append(repr(err))
         return {"error": repr(err)}
 
+    # single-GPU legs run at N = 1 only (in a scaling run they would hold every GPU)
+    solo = world == 1
+
     # wall-time budget of the whole run: a secondary leg starts only with `need` seconds
     # left (its caps shrink with the time left); per-leg seconds go into the line
     leg_s, skipped = {}, {}
@@ -805,8 +808,6 @@ def run_ours(args):
     fp64 = None
     t_leg = time.perf_counter()
     try:
-        # single-GPU legs run at N = 1 only (in a scaling run they would hold every GPU)
-        solo = world == 1
         if args.fp64_traj > 0 and solo and not dead and budget("fp64_path", 20):
             n64 = args.fp64_traj
             e64 = reg(lt.Ensemble(L, chi, n64, precision=lt.LT_FP64, init="neel",

@@ -2313,6 +2313,56 @@ __device__ __forceinline__ long long sum_prod(int a, int b, int r, bool linear =
   return R * A * B - (A + B) * s1 + s2;
 }
 
+// B_b = theta~ V_k (times invn) by a cluster, as the one-CTA split computes it: an item is
+// four rows of B_b and two of its columns; the items are dealt over the cluster's threads
+// (this CTA taking share `part` of `parts`), and every operand is read past L1.
+__device__ void split_rows_cluster(const float* Xr, const float* Xi, int ldp, int m, int nJ,
+                                   const float2* Y, int ld, int k, float invn, float2* Bl,
+                                   int part, int parts) {
+  const int rq = (m + 3) >> 2, kq = (k + 1) >> 1;
+  for (int idx = part * blockDim.x + threadIdx.x; idx < rq * kq; idx += parts * blockDim.x) {
+    const int g = idx / kq, r0 = g << 2, j0 = 2 * (idx - g * kq);
+    const bool two = j0 + 1 < k;
+    const float2* y0 = Y + j0 * ld;
+    const float2* y1 = Y + (two ? j0 + 1 : j0) * ld;
+    float2 acc[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = make_float2(0.f, 0.f);
+    const int nr = m - r0 < 4 ? m - r0 : 4;
+    for (int c = 0; c < nJ; ++c) {
+      const float2 v0 = __ldcg(y0 + c), v1 = __ldcg(y1 + c);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < nr) {
+          const long long o = (long long)(r0 + u) * ldp + c;
+          const float2 x = make_float2(__ldcg(Xr + o), __ldcg(Xi + o));
+          cfmac(acc[u][0], x, v0);
+          cfmac(acc[u][1], x, v1);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (u < nr) {
+        Bl[(r0 + u) * k + j0] = cscale(acc[u][0], invn);
+        if (two) Bl[(r0 + u) * k + j0 + 1] = cscale(acc[u][1], invn);
+      }
+  }
+}
+
+// The split's part of a helper CTA: rank 0 has re-formed theta~, finished V_k^+ and
+// published 1/|S_k|; every CTA computes its items of B_b; two cluster barriers.
+__device__ __noinline__ void cluster_split(const float* Xr, const float* Xi, int ldp, int m,
+                                           int nJ, const float2* Y, int ld, float2* Bl,
+                                           const float* cls, int crank, int C) {
+  __threadfence();
+  cluster_sync();  // theta~, V_k^+ and 1/|S_k| published
+  const int k = __ldcg(reinterpret_cast<const int*>(cls + LT_CL_K));
+  const float invn = __ldcg(cls + LT_CL_K + 1);
+  split_rows_cluster(Xr, Xi, ldp, m, nJ, Y, ld, k, invn, Bl, crank, C);
+  __threadfence();
+  cluster_sync();  // every item of B_b written
+}
+
 // The CTAs of rank > 0 of a cluster: they walk the tasks of their cluster like rank 0
 // and join exactly the Jacobis that rank 0 shares (tasks in global scratch with rows
 // of more than 128 columns); everything else of a task is rank 0's.
@@ -2343,7 +2393,11 @@ __device__ __noinline__ void cluster_helper(const BondArgs<float>& a, float* s_n
     if (cl_pre) precondition_cluster(Xr, Xi, lay.ldp, lay.mJ, lay.nJ, Y, cls, crank, C);
     wide_jacobi(Xr, Xi, lay.ldp, lay.mp2, lay.rr, lay.npad2, s_nrm, s_part, s_nrot, a.max_sweeps,
                 a.tol, C, crank, cls);
-    if (cl_pre) cluster_q1(Xr, Xi, lay.ldp, lay.nJ, lay.rr, Y, cls, crank, C);
+    if (cl_pre) {
+      cluster_q1(Xr, Xi, lay.ldp, lay.nJ, lay.rr, Y, cls, crank, C);
+      float2* Bl = a.B + ((long long)traj * L + b) * a.slot;
+      cluster_split(Xr, Xi, lay.ldp, D * chiL, lay.nJ, Y, lay.ld, Bl, cls, crank, C);
+    }
   }
 }
 
@@ -2631,7 +2685,22 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
       // columns j, j + 1, so each load of theta~ feeds two products and each load of V_k^+
       // four
       const int rq = (m + 3) >> 2, kq = (k + 1) >> 1;
-      for (int idx = tid; idx < rq * kq; idx += blockDim.x) {
+      if constexpr (kCl) {
+        if (shared_jac && cluster_shares_precondition(mJ, nJ)) {
+          // the cluster computes B_b's items (rank 0's share here, the rest in cluster_split)
+          float* cls = a.cl_state + cid * LT_CL_STATE;
+          if (tid == 0) cls[LT_CL_K + 1] = invn;
+          __threadfence();
+          cluster_sync();
+          split_rows_cluster(reinterpret_cast<const float*>(Xr), reinterpret_cast<const float*>(Xi),
+                             ldp, m, nJ, reinterpret_cast<const float2*>(Y), ld, k, invn,
+                             reinterpret_cast<float2*>(Bl), 0, C);
+          __threadfence();
+          cluster_sync();
+        }
+      }
+      const bool split_here = !(kCl && shared_jac && cluster_shares_precondition(mJ, nJ));
+      for (int idx = tid; split_here && idx < rq * kq; idx += blockDim.x) {
         const int g = idx / kq, r0 = g << 2, j0 = 2 * (idx - g * kq);
         const bool two = j0 + 1 < k;
         const Tc* y0 = Y + j0 * ld;
