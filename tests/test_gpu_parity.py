@@ -485,20 +485,23 @@ def test_chi256_theta_512(precision, tol):
         assert list(gd[0]) == ref.bond_dims()
 
 
+@pytest.mark.parametrize("method", ["trajectory", "qsd"])
 @pytest.mark.parametrize("chi", [128, 256])
-def test_cluster_launch_equals_the_one_cta_launch_pure_state(chi):
+def test_cluster_launch_equals_the_one_cta_launch_pure_state(chi, method):
     # One 18-site trajectory at chi_max = 128 or 256 (theta up to 256 or 512) gives a
     # layer 9 tasks: its single-precision layers go out as thread-block clusters that
-    # share the wide Jacobi; within 16 trajectories (144 tasks) each task has one CTA.
-    # Same block rounds, same arithmetic: equal bit for bit.
+    # share the wide Jacobi, the preconditioning, V_k^+ and the split; within 16
+    # trajectories (144 tasks) each task has one CTA.  Same arithmetic: equal bit for
+    # bit.  QSD keeps the norm change in B_b (the split is not rescaled).
     lt = _lt()
     L = 18
     dims = [min(2 ** (b + 1), 2 ** (L - b - 1), chi) for b in range(L - 1)]
     B, lam, dims = workloads.synthetic_mps(L, chi, seed=21, dims=dims)
+    kw = dict(method=lt.LT_QSD, gamma_deph=0.1, fermionic_jumps=0) if method == "qsd" else {}
     runs = []
     for n in (1, 16):
         with lt.Ensemble(L, chi, n, precision=lt.LT_MIXED, dt=0.02, gamma_loss=0.2,
-                         svd_cut=1e-6) as e:
+                         svd_cut=1e-6, **kw) as e:
             e.set_state(0, [(B, lam, dims)] * n)
             e.apply_layer(0, 0.02)
             e.apply_layer(1, 0.02)

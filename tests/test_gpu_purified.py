@@ -185,3 +185,28 @@ def test_configured_chi96_theta_384(precision, tol):
         assert err < tol, "bond %d: relative error %.2e" % (b, err)
     if precision == "fp64":
         assert list(gd[0]) == ref.bond_dims()
+
+
+def test_cluster_launch_equals_the_one_cta_launch():
+    # one chain: its single-precision layers go out as thread-block clusters that share
+    # the wide Jacobi, the preconditioning, V_k^+ and the split of the 384 x 384 theta (the
+    # purified form keeps the norm change, so the split is not rescaled); inside 96 chains
+    # each task has one CTA.  The same arithmetic either way: equal bit for bit.
+    lt = _lt()
+    L, chi = 10, 96
+    dims = [4, 16, 64, 96, 96, 96, 64, 16, 4]
+    B, lam, dims = workloads.synthetic_mps(L, chi, seed=23, d=4, dims=dims)
+    cfg = cfg_of(L, chi, loss=0.1, deph=0.05, cut=1e-6)
+    runs = []
+    for n in (1, 96):
+        with ensemble(cfg, n, lt.LT_MIXED) as e:
+            e.set_state(0, [(B, lam, dims)] * n)
+            e.apply_layer(0, 0.01)
+            e.apply_layer(1, 0.01)
+            runs.append((e.get_state(0, 1), lt.lt_cluster_launches(e.ctx)))
+    (d1, l1, b1), c1 = runs[0]
+    (d2, l2, b2), c2 = runs[1]
+    assert c1 == 2 and c2 == 0
+    assert np.array_equal(d1, d2)
+    assert np.array_equal(l1, l2)
+    assert np.array_equal(b1, b2)
