@@ -933,9 +933,11 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 c8 = e8.counters()
                 s8 = a.elapsed_time(b) / 1e3
+                tf8 = (c8["layer_flops"] + c8["sweep_flops"]) / s8 / 1e12
                 qsd["chi128"] = {"histories": n8, "steps": 1, "ms_per_step": 1e3 * s8,
                                  "updates_per_s": c8["updates"] / s8,
-                                 "layer_updates_per_s": c8["layer_updates"] / s8}
+                                 "layer_updates_per_s": c8["layer_updates"] / s8,
+                                 "bond_kernel_tflops": tf8, "alu_frac": tf8 / alu_peak}
                 e8.close()
                 del m8, p8
             # the QSD configuration as written: L=128, chi_max=128, 1024 histories from
