@@ -391,8 +391,9 @@ int64_t lt_launch_count(lt_ctx ctx);
 /* Number of those launches made as thread-block clusters: a single-precision Trotter
  * layer with few tasks whose theta can exceed 128 x 128 (a launch of n_traj x bonds
  * tasks when that many clusters of 2, 4 or 8 CTAs fit the device at once) gives each
- * task a cluster, whose CTAs share the task's Jacobi sweeps; the results are those of
- * the one-CTA launch. */
+ * task a cluster, whose CTAs share the task's Jacobi sweeps and, when theta is no
+ * taller than wide, its preconditioning, V_k^+ and split; the results are those of the
+ * one-CTA launch bit for bit. */
 int64_t lt_cluster_launches(lt_ctx ctx);
 
 /* The context's CUDA stream (a cudaStream_t). */
