@@ -2300,7 +2300,8 @@ __global__ void __launch_bounds__(512, 1) theta_tc_kernel(BondArgs<float> a) {
 //         a one-site SVD): B_{b+1} = U S V^+ (chi_b x 2chi_{b+1}), B_{b+1} = V_k^+,
 //         B_b = B_b B_{b+1} V_k (= B_b U_k S_k), no renormalisation.
 // mode 2: restore bond b: Lambda_{b-1} B_b = U S V^+ (2chi_{b-1} x chi_b),
-//         Lambda_b = S_k/|S_k|, B_b = B_b V_k / |S_k|, B_{b+1} = V_k^+ B_{b+1}.
+//         B_b = B_b V_k / |S_k|, B_{b+1} = V_k^+ B_{b+1}, Lambda_b = the column
+//         norms of Lambda_{b-1} B_b (= S_k/|S_k| in exact arithmetic).
 // Workspace (shared memory, or per-CTA global scratch when it does not fit):
 // the Jacobi matrix planar (2 mcap ldp reals; in mode 0/1 later theta~), then
 // V_k^+ rows (k x (nJ+1) complex); in mode 0 the region after theta first
@@ -2745,6 +2746,22 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
         St[idx] = cscale(acc, invn);
       }
       __syncthreads();
+      // Lambda_b as the norms of the columns of Lambda_{b-1} B_b that are stored
+      // (accumulated in double): S_k/|S_k| in exact arithmetic, and in single
+      // precision the norm the new tensors carry, which S_k from the rotated
+      // columns misstates by a bias that the sweep would pass into <psi|psi>
+      {
+        double* lb = a.lam + ((long long)traj * (L - 1) + b) * chi;
+        for (int j = tid; j < k; j += blockDim.x) {
+          double s = 0.0;
+          for (int r = 0; r < m; ++r) {
+            const double w = s_lamL[D == 2 ? r >> 1 : r / D];
+            const Tc x = St[r * k + j];
+            s += w * w * ((double)x.x * (double)x.x + (double)x.y * (double)x.y);
+          }
+          lb[j] = sqrt(s);
+        }
+      }
       for (int idx = tid; idx < m * k; idx += blockDim.x) Bl[idx] = St[idx];
       __syncthreads();
       // B_{b+1} <- V_k^+ B_{b+1} (k x 2chi_{b+1}), staged, then written
@@ -2760,7 +2777,7 @@ __global__ void __launch_bounds__(BondShape<R>::NT, 1) bond_update_kernel(BondAr
     }
     {
       double* lb = a.lam + ((long long)traj * (L - 1) + b) * chi;
-      for (int j = tid; j < k; j += blockDim.x) lb[j] = sqrt(s_sig[s_perm[j]]) / s_norm;
+      for (int j = tid; mode != 2 && j < k; j += blockDim.x) lb[j] = sqrt(s_sig[s_perm[j]]) / s_norm;
       if (tid == 0) {
         a.dims[(long long)traj * (L - 1) + b] = k;
         if (mode != 1) a.trunc[(long long)traj * (L - 1) + b] += s_wdisc;

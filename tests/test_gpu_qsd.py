@@ -91,6 +91,34 @@ def test_qsd_mixed_histories(qsd_oracle):
     close(mean, want_mean, 2e-5, "mixed weighted estimator")
 
 
+def test_qsd_mixed_log_weight_does_not_drift():
+    # ln <psi|psi> of single-precision histories against the FP64 path on the same
+    # Philox noise (32 sites, spin loss and dephasing everywhere, 40 steps).  The
+    # single-precision steps bias the norm the same way in every history, so the
+    # mean difference grows step by step; measured -3.9e-5 after 40 steps (2.5e-5
+    # of it from step 20 on).  Taking the restored Schmidt spectrum from the singular
+    # values instead of from the norms of the tensors the sweep stores doubles it
+    # (-7.7e-5, 5.0e-5 from step 20 on), which these bounds reject.
+    cfg = qsd_cfg(32, 64, dt=0.01, loss=0.05, deph=0.1, fermionic=False)
+    n, marks = 32, (10, 20, 30, 40)
+    lt = _lt()
+    logw = {}
+    for prec in (lt.LT_FP64, lt.LT_MIXED):
+        with gpu_qsd(cfg, n, prec, cut=1e-6) as ens:
+            for s in range(marks[-1]):
+                for parity, tau in cfg.layers():
+                    ens.apply_layer(parity, tau)
+                ens.apply_noise(s)
+                if s + 1 in marks:
+                    logw[prec, s + 1] = ens.log_weights().copy()
+    d = [logw[lt.LT_MIXED, t] - logw[lt.LT_FP64, t] for t in marks]
+    mean = [float(x.mean()) for x in d]
+    print("mixed - FP64 ln w, mean over histories at steps", marks, mean,
+          "max", float(np.abs(d[-1]).max()))
+    assert np.abs(logw[lt.LT_FP64, marks[-1]]).max() > 1e-2, "the weights should move"
+    assert abs(mean[-1]) <= 5e-5 and abs(mean[-1] - mean[1]) <= 3.5e-5, mean
+
+
 def test_qsd_spin_loss_from_truncated_synthetic_states():
     # spin loss on every site (local), dephasing, ragged start states, chi = 8
     # truncation active
