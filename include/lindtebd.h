@@ -177,7 +177,11 @@ lt_status lt_gates(const lt_config* cfg, double tau, double* out, int64_t capaci
  * (traj_offset + traj, step, 1 + j, step >> 32) and key seed, k = 3 site +
  * kind.  It then restores the exact canonical form of every history (one-site
  * SVDs right to left, then left to right) and adds ln <psi|psi>, found at bond
- * 0, to the history's log weight (lt_get_log_weights).  Only site-local L_k are
+ * 0, to the history's log weight (lt_get_log_weights).  The left-to-right pass
+ * (also the one after a jump) stores Lambda_b as the norms of the columns of
+ * Lambda_{b-1} B_b as stored, accumulated in double: the normalised singular
+ * values in exact arithmetic, and in single precision the norm the stored
+ * tensors carry.  Only site-local L_k are
  * accepted: lt_create returns LT_ERR_UNSUPPORTED for an LT_QSD context with
  * fermionic loss or gain beyond site 0 (the string would make the factor a sum
  * of non-local products). */
