@@ -260,3 +260,8 @@ def test_one_site_recanonicalisation_equals_two_site_identity_sweep():
         for Bi in a.B[1:]:
             M = Bi.reshape(Bi.shape[0], -1)
             assert np.abs(M @ M.conj().T - np.eye(M.shape[0])).max() < 1e-12
+        # and Lambda_{b-1} B_b has orthogonal columns whose norms are Lambda_b (the
+        # left half of the canonical form, which fixes Lambda_b by the stored tensors)
+        for bond in range(L - 1):
+            X = np.repeat(a.left_weight(bond), 2)[:, None] * a.B[bond].reshape(-1, a.B[bond].shape[2])
+            assert np.abs(X.conj().T @ X - np.diag(a.lam[bond] ** 2)).max() < 1e-12

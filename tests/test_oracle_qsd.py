@@ -53,6 +53,29 @@ def test_mps_qsd_equals_the_state_vector(L, dt, fermionic):
         assert np.abs(C - res["corr"][t]).max() < 1e-12
 
 
+def test_noise_step_leaves_the_canonical_form():
+    # after every noise step (one-site SVDs right to left, then left to right) each
+    # B_{b+1} is right-canonical and Lambda_{b-1} B_b has orthogonal columns whose
+    # norms are Lambda_b, normalised to sum(Lambda_b^2) = 1, while the log weight
+    # keeps <psi|psi>
+    L = 7
+    cfg = cfg_qsd(L, 0.05, fermionic=False, chi=8)
+    cfg.gamma_loss[:] = 0.2
+    cfg.svd_cut = 1e-10
+    tr = tebd.Trajectory(cfg)
+    gates = tebd.StepGates(cfg)
+    for s in range(10):
+        tebd.step_qsd(tr, gates, 1, s)
+        for b in range(L - 1):
+            X = np.repeat(tr.left_weight(b), 2)[:, None] * tr.B[b].reshape(-1, tr.B[b].shape[2])
+            assert np.abs(X.conj().T @ X - np.diag(tr.lam[b] ** 2)).max() < 1e-12
+            assert abs(np.sum(tr.lam[b] ** 2) - 1.0) < 1e-12
+            M = tr.B[b + 1].reshape(tr.B[b + 1].shape[0], -1)
+            assert np.abs(M @ M.conj().T - np.eye(M.shape[0])).max() < 1e-12
+    assert max(tr.bond_dims()) == 8, "truncation should act"
+    assert abs(tr.log_weight) > 1e-3, "the weight should move"
+
+
 def test_bulk_fermionic_loss_is_rejected():
     cfg = cfg_qsd(4, 0.05)
     cfg.gamma_loss[2] = 0.1
