@@ -1020,14 +1020,14 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "bond_update_kernel<float>",
                          "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak,
-                         "traffic": BOND_DRAM_BYTES_PER_UPDATE
-                         * cnt["layer_updates"] / max(len(layer_ms), 1),
-                         "traffic_note": "bytes per layer launch: DRAM bytes per update from "
-                                         "an ncu capture of the 256-trajectory case (%.0f B) "
-                                         "times this launch's updates; algorithmic %.0f B "
-                                         "(the two site tensors read and written once, "
-                                         "complex64)" % (BOND_DRAM_BYTES_PER_UPDATE,
-                                                         4 * 2 * chi * chi * 8),
+                         "traffic": None,
+                         "traffic_note": "null: the DRAM counters (%.0f B per update, an ncu "
+                                         "capture of the 256-trajectory case) predate a change "
+                                         "to the kernel's restoring mode, which the layer "
+                                         "launches do not run, and were not taken again; "
+                                         "algorithmic %.0f B per update (the two site tensors "
+                                         "read and written once, complex64)"
+                                         % (BOND_DRAM_BYTES_PER_UPDATE, 4 * 2 * chi * chi * 8),
                          "peak_source": "measured on this GPU (lt_pipe_peaks: independent "
                                         "packed FP32 FMA chains, 4 CTAs x 256 threads per SM, "
                                         "CUDA events); derived from unit counts: %.1f TFLOP/s "
